@@ -1,0 +1,343 @@
+/*
+ * qw_oracle.c -- plain, slow, FP64 CPU oracle for the discrete-time coined
+ * quantum walk on the cycle Z_N (coin dim 2) and the torus Z_Lx x Z_Ly
+ * (coin dim 4).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline / reference arm may load this file.  It shares no
+ * code, header, table or helper with the CUDA library; it is written directly
+ * from the definitions in Sawerwain & Gielerak, "GPGPU based simulations for
+ * one and two dimensional quantum walks" (arXiv:1003.3779):
+ *
+ *   Sec. 2.1   coin flip transformation C_v acting on the local space of v,
+ *              one-step operator U = S (I (x) C), shift S|v,e> = |v',e>.
+ *   Sec. 2.2   Z^1 walk on l2(Z) (x) C^2, Z^2 walk on l2(Z^2) (x) C^4,
+ *              normalised amplitudes (sum of |alpha|^2 equals 1).
+ *   Sec. 3     U = S (C (x) I) restated for the 2D state with two coin
+ *              qubits, shift operator (eq. "shift operator"), random broken
+ *              links (the RBL function), segment vs. line boundary.
+ *
+ * Conventions (readings of the paper, each listed in the design notes):
+ *   - state: d coin-major planes, plane c holds nsites complex amplitudes
+ *     (re, im interleaved doubles), site index v = x (1D) or v = y*Lx + x (2D);
+ *   - 1D directions: coin 0 moves x -> x-1, coin 1 moves x -> x+1;
+ *   - 2D directions: coin 0: +x, 1: -x, 2: +y, 3: -y;
+ *   - moving shift:    S|v,c> = |v + e_c, c>
+ *     flip-flop shift: S|v,c> = |v + e_c, c xor 1>
+ *   - a closed link (RBL) reflects: the amplitude stays on its site and
+ *     takes the one coin slot the closed link leaves empty, which keeps S a
+ *     permutation of basis states: S|v,c> = |v, c xor 1> for the moving
+ *     shift, S|v,c> = |v, c> for the flip-flop shift (whose open move already
+ *     flips the coin); a link that crosses the lattice edge is periodic (bc 0),
+ *     closed (bc 1, "segment") or absorbing (bc 2, "line": the amplitude
+ *     leaves the finite window of the infinite lattice and is dropped);
+ *   - coin modes: 0 one global d x d matrix; 1 one matrix per site;
+ *     2 per-site phases, C_v = B . diag(exp(i phi_{v,k})) (phase first).
+ *
+ * Every step is the push form of the definition: first the coin at every
+ * site, phi_v = C_v psi_v, then every amplitude is sent along the shift map.
+ * The adjoint step applies the transpose of the same map, then C_v^dagger.
+ * No blocking, fusion or reordering beyond that.  Floating point: IEEE
+ * double, compiled with -ffp-contract=off.
+ */
+#include <complex.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+typedef double complex cplx;
+
+enum { OR_OK = 0, OR_EINVAL = -1, OR_ENOMEM = -2 };
+
+/* Lattice description shared by the routines below. */
+typedef struct {
+    int ndim;          /* 1 or 2 */
+    int64_t nx, ny;    /* extent in x and y (ny = 1 in 1D) */
+    int64_t nsites;    /* nx * ny */
+    int d;             /* coin dimension: 2 (1D) or 4 (2D) */
+    int shift;         /* 0 moving, 1 flip-flop */
+    int bc;            /* 0 periodic, 1 segment (reflect), 2 line (absorb) */
+    const uint8_t *closed; /* NULL, or ndim*nsites link flags (RBL) */
+    int coin_mode;     /* 0 global, 1 per-site matrices, 2 per-site phases */
+    const double *coin;/* complex, row-major d x d (mode 0 and 2) or nsites*d*d */
+    const double *phi; /* nsites*d reals (mode 2) */
+} lattice;
+
+static int lattice_init(lattice *L, int ndim, const int64_t *dims, int shift,
+                        int bc, const uint8_t *closed, int coin_mode,
+                        const double *coin, const double *phi)
+{
+    if (ndim != 1 && ndim != 2) return OR_EINVAL;
+    if (!dims || dims[0] < 1 || (ndim == 2 && dims[1] < 1)) return OR_EINVAL;
+    if (shift != 0 && shift != 1) return OR_EINVAL;
+    if (bc < 0 || bc > 2) return OR_EINVAL;
+    if (coin_mode < 0 || coin_mode > 2 || !coin) return OR_EINVAL;
+    if (coin_mode == 2 && !phi) return OR_EINVAL;
+    L->ndim = ndim;
+    L->nx = dims[0];
+    L->ny = ndim == 2 ? dims[1] : 1;
+    L->nsites = L->nx * L->ny;
+    L->d = 2 * ndim;
+    L->shift = shift;
+    L->bc = bc;
+    L->closed = closed;
+    L->coin_mode = coin_mode;
+    L->coin = coin;
+    L->phi = phi;
+    return OR_OK;
+}
+
+/* Coin C_v as a d x d complex matrix, row-major (Sec. 2.1: the coin flip
+ * transformation C_v acts on the local space of site v). */
+static void coin_at(const lattice *L, int64_t v, cplx *C)
+{
+    const int d = L->d;
+    const double *m = L->coin;
+    if (L->coin_mode == 1) m += (size_t)v * d * d * 2;
+    for (int r = 0; r < d; ++r)
+        for (int c = 0; c < d; ++c)
+            C[r * d + c] = m[2 * (r * d + c)] + I * m[2 * (r * d + c) + 1];
+    if (L->coin_mode == 2) {
+        /* C_v = B . diag(e^{i phi_{v,k}}): column k of B times e^{i phi_{v,k}} */
+        for (int c = 0; c < d; ++c) {
+            double a = L->phi[(size_t)v * d + c];
+            cplx e = cos(a) + I * sin(a);
+            for (int r = 0; r < d; ++r) C[r * d + c] = C[r * d + c] * e;
+        }
+    }
+}
+
+/* Where the shift sends the basis state |v, c>.  Returns 1 and sets
+ * (*vo, *co) when the amplitude lands somewhere, 0 when it is absorbed
+ * (line boundary).  Directions: 1D coin 0 -> x-1, coin 1 -> x+1; 2D coin 0
+ * +x, 1 -x, 2 +y, 3 -y.  The link used by a move from (x,y) in direction +x
+ * is x-link (x,y); in direction -x it is x-link (x-1,y); same for y.  The
+ * x-links occupy closed[0 .. nsites), the y-links closed[nsites .. 2 nsites). */
+static int shift_map(const lattice *L, int64_t v, int c, int64_t *vo, int *co)
+{
+    int64_t x = v % L->nx, y = v / L->nx;
+    int axis, sgn;
+    if (L->ndim == 1) { axis = 0; sgn = (c == 0) ? -1 : +1; }
+    else { axis = c >> 1; sgn = (c & 1) ? -1 : +1; }
+    int64_t n = axis == 0 ? L->nx : L->ny;
+    int64_t p = axis == 0 ? x : y;
+    /* the link between p and p+1 is indexed by p; moving -1 uses link p-1 */
+    int64_t lp = sgn > 0 ? p : (p - 1 + n) % n;
+    int64_t lx = axis == 0 ? lp : x, ly = axis == 0 ? y : lp;
+    int closed = 0;
+    if (L->closed) closed = L->closed[(size_t)axis * L->nsites + ly * L->nx + lx] != 0;
+    int crosses_edge = (lp == n - 1);   /* link (n-1) -- 0 wraps the lattice */
+    if (crosses_edge && L->bc == 1) closed = 1;
+    if (closed) { *vo = v; *co = L->shift == 1 ? c : (c ^ 1); return 1; }
+    if (crosses_edge && L->bc == 2) return 0;
+    int64_t q = (p + sgn + n) % n;
+    if (axis == 0) x = q; else y = q;
+    *vo = y * L->nx + x;
+    *co = L->shift == 1 ? (c ^ 1) : c;
+    return 1;
+}
+
+static void load_state(const lattice *L, const double *psi, cplx *s)
+{
+    for (int c = 0; c < L->d; ++c)
+        for (int64_t v = 0; v < L->nsites; ++v) {
+            const double *p = psi + 2 * ((size_t)c * L->nsites + v);
+            s[(size_t)v * L->d + c] = p[0] + I * p[1];
+        }
+}
+
+static void store_state(const lattice *L, const cplx *s, double *psi)
+{
+    for (int c = 0; c < L->d; ++c)
+        for (int64_t v = 0; v < L->nsites; ++v) {
+            double *p = psi + 2 * ((size_t)c * L->nsites + v);
+            cplx a = s[(size_t)v * L->d + c];
+            p[0] = creal(a);
+            p[1] = cimag(a);
+        }
+}
+
+/* One step of U = S (I (x) C) (Sec. 2.1).  in/out are site-major d-vectors. */
+static void step_forward(const lattice *L, const cplx *in, cplx *out)
+{
+    const int d = L->d;
+    memset(out, 0, sizeof(cplx) * (size_t)L->nsites * d);
+    #pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < L->nsites; ++v) {
+        cplx C[16], phi[4];
+        coin_at(L, v, C);
+        for (int r = 0; r < d; ++r) {
+            cplx acc = 0;
+            for (int c = 0; c < d; ++c) acc += C[r * d + c] * in[(size_t)v * d + c];
+            phi[r] = acc;
+        }
+        /* the shift is a bijection of basis states (or drops an amplitude),
+         * so every target slot receives from exactly one source: no races */
+        for (int c = 0; c < d; ++c) {
+            int64_t vo; int co;
+            if (shift_map(L, v, c, &vo, &co)) out[(size_t)vo * d + co] = phi[c];
+        }
+    }
+}
+
+/* One step of U^dagger = (I (x) C^dagger) S^dagger: S^dagger gathers along
+ * the same map that S scatters along, then each site applies C_v^dagger. */
+static void step_adjoint(const lattice *L, const cplx *in, cplx *out)
+{
+    const int d = L->d;
+    #pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < L->nsites; ++v) {
+        cplx C[16], g[4];
+        for (int c = 0; c < d; ++c) {
+            int64_t vo; int co;
+            g[c] = shift_map(L, v, c, &vo, &co) ? in[(size_t)vo * d + co] : 0;
+        }
+        coin_at(L, v, C);
+        for (int r = 0; r < d; ++r) {
+            cplx acc = 0;
+            for (int c = 0; c < d; ++c) acc += conj(C[c * d + r]) * g[c];
+            out[(size_t)v * d + r] = acc;
+        }
+    }
+}
+
+/* psi_out = U^T psi_in (adjoint = 0) or (U^dagger)^T psi_in (adjoint = 1).
+ * psi_in and psi_out: d coin-major planes of nsites complex doubles; they may
+ * alias.  closed: NULL or ndim*nsites link flags; closed_per_step != 0 means
+ * closed holds T consecutive such masks, mask t used by step t (for the
+ * adjoint run, step t applies the adjoint of forward step T-1-t). */
+int oracle_evolve(int ndim, const int64_t *dims, int shift, int bc,
+                  const uint8_t *closed, int closed_per_step,
+                  int coin_mode, const double *coin, const double *phi,
+                  const double *psi_in, int64_t T, int adjoint, double *psi_out)
+{
+    lattice L;
+    int st = lattice_init(&L, ndim, dims, shift, bc, closed, coin_mode, coin, phi);
+    if (st) return st;
+    if (T < 0 || !psi_in || !psi_out) return OR_EINVAL;
+    size_t n = (size_t)L.nsites * L.d;
+    cplx *a = malloc(sizeof(cplx) * n), *b = malloc(sizeof(cplx) * n);
+    if (!a || !b) { free(a); free(b); return OR_ENOMEM; }
+    load_state(&L, psi_in, a);
+    for (int64_t t = 0; t < T; ++t) {
+        if (closed && closed_per_step) {
+            int64_t m = adjoint ? (T - 1 - t) : t;
+            L.closed = closed + (size_t)m * ndim * L.nsites;
+        }
+        if (adjoint) step_adjoint(&L, a, b); else step_forward(&L, a, b);
+        cplx *tmp = a; a = b; b = tmp;
+    }
+    store_state(&L, a, psi_out);
+    free(a); free(b);
+    return OR_OK;
+}
+
+/* P(v) = sum_c |psi(v,c)|^2 (the normalisation sums of Sec. 2.2, per site),
+ * norm = sum_v P(v) with Neumaier-compensated summation in site order. */
+int oracle_probabilities(int ndim, const int64_t *dims, const double *psi,
+                         double *P, double *norm)
+{
+    if ((ndim != 1 && ndim != 2) || !dims || !psi) return OR_EINVAL;
+    int64_t ns = dims[0] * (ndim == 2 ? dims[1] : 1);
+    int d = 2 * ndim;
+    double s = 0.0, comp = 0.0;
+    for (int64_t v = 0; v < ns; ++v) {
+        double p = 0.0;
+        for (int c = 0; c < d; ++c) {
+            const double *a = psi + 2 * ((size_t)c * ns + v);
+            p += a[0] * a[0] + a[1] * a[1];
+        }
+        if (P) P[v] = p;
+        double t = s + p;
+        if (fabs(s) >= fabs(p)) comp += (s - t) + p; else comp += (p - t) + s;
+        s = t;
+    }
+    if (norm) *norm = s + comp;
+    return OR_OK;
+}
+
+/* Gradient of the region mass L = sum_{v in R, c} |psi_T(v,c)|^2 with respect
+ * to the per-site coin phases phi_{v,k}, for C_v = B . diag(e^{i phi_{v,k}})
+ * on the 2D torus (coin mode 2).  Stored-trajectory form: psi_0 .. psi_T are
+ * all kept.  With lambda_T = 1_R psi_T and lambda_t = U^dagger lambda_{t+1}:
+ *     a_t = B^dagger S^dagger lambda_{t+1}  (at site v),
+ *     b_t = diag(e^{i phi_v}) psi_t(v),
+ *     dL/dphi_{v,k} = sum_t -2 Im( conj(a_t[k]) b_t[k] ).
+ * rect = {x0, y0, w, h}: the sites x0 <= x < x0+w, y0 <= y < y0+h.
+ * grad: nsites*d doubles, site-major (grad[v*d + k]). */
+int oracle_region_grad(const int64_t *dims, int shift, const double *base,
+                       const double *phi, const double *psi0, int64_t T,
+                       const int64_t *rect, double *loss, double *grad)
+{
+    lattice L;
+    int st = lattice_init(&L, 2, dims, shift, 0, NULL, 2, base, phi);
+    if (st) return st;
+    if (T < 0 || !psi0 || !rect || !grad) return OR_EINVAL;
+    if (rect[0] < 0 || rect[1] < 0 || rect[2] < 0 || rect[3] < 0 ||
+        rect[0] + rect[2] > L.nx || rect[1] + rect[3] > L.ny) return OR_EINVAL;
+    const int d = 4;
+    size_t n = (size_t)L.nsites * d;
+    cplx *traj = malloc(sizeof(cplx) * n * (size_t)(T + 1));
+    cplx *lam = malloc(sizeof(cplx) * n), *nxt = malloc(sizeof(cplx) * n);
+    if (!traj || !lam || !nxt) { free(traj); free(lam); free(nxt); return OR_ENOMEM; }
+    load_state(&L, psi0, traj);
+    for (int64_t t = 0; t < T; ++t) step_forward(&L, traj + n * t, traj + n * (t + 1));
+
+    const cplx *psiT = traj + n * T;
+    double l = 0.0;
+    memset(lam, 0, sizeof(cplx) * n);
+    for (int64_t y = rect[1]; y < rect[1] + rect[3]; ++y)
+        for (int64_t x = rect[0]; x < rect[0] + rect[2]; ++x) {
+            int64_t v = y * L.nx + x;
+            for (int c = 0; c < d; ++c) {
+                cplx a = psiT[(size_t)v * d + c];
+                lam[(size_t)v * d + c] = a;
+                l += creal(a) * creal(a) + cimag(a) * cimag(a);
+            }
+        }
+    if (loss) *loss = l;
+    memset(grad, 0, sizeof(double) * n);
+
+    cplx B[16];
+    for (int r = 0; r < d; ++r)
+        for (int c = 0; c < d; ++c)
+            B[r * d + c] = base[2 * (r * d + c)] + I * base[2 * (r * d + c) + 1];
+
+    for (int64_t t = T - 1; t >= 0; --t) {
+        const cplx *psit = traj + n * t;
+        for (int64_t v = 0; v < L.nsites; ++v) {
+            cplx mu[4], a[4];
+            for (int c = 0; c < d; ++c) {
+                int64_t vo; int co;
+                mu[c] = shift_map(&L, v, c, &vo, &co) ? lam[(size_t)vo * d + co] : 0;
+            }
+            for (int r = 0; r < d; ++r) {
+                cplx acc = 0;
+                for (int c = 0; c < d; ++c) acc += conj(B[c * d + r]) * mu[c];
+                a[r] = acc;
+            }
+            for (int k = 0; k < d; ++k) {
+                double ph = phi[(size_t)v * d + k];
+                cplx e = cos(ph) + I * sin(ph);
+                cplx b = e * psit[(size_t)v * d + k];
+                grad[(size_t)v * d + k] += -2.0 * cimag(conj(a[k]) * b);
+                nxt[(size_t)v * d + k] = conj(e) * a[k];
+            }
+        }
+        cplx *tmp = lam; lam = nxt; nxt = tmp;
+    }
+    free(traj); free(lam); free(nxt);
+    return OR_OK;
+}
+
+/* Number of threads the OpenMP build runs with (1 without OpenMP). */
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
