@@ -1,0 +1,437 @@
+"""Benchmark of the coined quantum-walk hot path on GB300.
+
+Workload (one "step" of the benchmark = one pass of the whole path): the 1D walk
+on a cycle of N = 2^27 sites with the SU(2) coin theta = pi/4 (phases 0), a
+seeded random normalised state (complex64), T = 4096 walk steps with the
+temporal-blocking depth chosen by the autotuner, then the coin marginals
+P(x) and the norm.  Per benchmark step: the state is re-seeded from a resident
+device copy (set_state), stepped T times (fused coin + shift kernels, k steps
+per HBM round trip) and reduced to P (float32) and the norm (double).
+
+Metric: site-coin-updates/s = N * d * T / time (d = 2), whole job over all ranks.
+Also reported: the roofline of the dominant kernel (live CUDA-event timing),
+the FP64 / bf16-storage / compensated forms on the same input with their L1
+distance to the FP64 result, an end-to-end number through the C ABI with host
+buffers, the SM clocks during the timed region, and the FP64 CPU oracle timed
+on the host cores on a bounded sample (``cpu_baseline``).
+
+``--impl reference`` times that oracle alone (the reference arm).
+Multi-GPU (torchrun): independent replicas, one per GPU, no collective on the
+data path ("weak" scaling); a barrier and a max-over-ranks of the time only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "site-coin-updates/s and % HBM roofline, FP32 vs FP64 plain, at stated L1 err"
+UNIT = "site-coin-updates/s"
+N_SITES = 1 << 27
+T_STEPS = 4096
+THETA = math.pi / 4
+SEED = 1
+WORKLOAD = "1D SU(2) walk, cycle N=2^27, theta=pi/4, T=4096, random normalised complex64 state (seed 1)"
+
+SMS, FP32_LANES = 152, 128
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p["hbm_gbs"], p.get("sm_max_mhz", 2070.0), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+# ------------------------------------------------------------------ distributed helpers
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def init_dist(world, backend):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, value, device=None):
+    """Maximum of a float over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device=f"cuda:{device}" if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_throughput(units_per_rank, max_seconds, world):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / max_seconds
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        try:
+            self.f.close()
+        except Exception:
+            pass
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            rows = []
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for i, n in enumerate(names):
+                if len(r) > 5 + i and "Active" in r[5 + i] and "Not" not in r[5 + i]:
+                    reasons.add(n)
+        loaded = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle (baseline)
+def cpu_oracle_sample(target_s=12.0):
+    """Time the FP64 oracle (OpenMP build, all host cores) on a bounded sample of
+    the workload: the same coin and random-state recipe on a cycle of 2^22
+    sites, as many steps as fit in ~target_s seconds."""
+    import oracle
+    from paper_1003_3779_gb300 import inputs
+    n = 1 << 22
+    psi = inputs.random_state((2, n), seed=SEED)
+    C = inputs.su2(THETA)
+    oracle.evolve(psi, C, 1, openmp=True)            # warm-up / page-in
+    t0 = time.perf_counter()
+    oracle.evolve(psi, C, 1, openmp=True)
+    t1 = time.perf_counter() - t0
+    steps = max(2, min(64, int(target_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.evolve(psi, C, steps, openmp=True)
+    dt = time.perf_counter() - t0
+    return {"value": 2.0 * n * steps / dt, "unit": UNIT, "cores": oracle.num_threads(True),
+            "kind": "oracle",
+            "sample": f"FP64 oracle (C, OpenMP) on a cycle of 2^22 sites, same coin and state "
+                      f"recipe, {steps} steps in {dt:.2f} s"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("k_step1d.cuh", "qw_internal.cuh", "launch_step.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1003_3779_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the 1D step kernel from the committed ncu summary,
+    or None when the summary is missing or was taken on different kernel sources."""
+    p = os.path.join(ROOT, "profiles", "k_step1d_su2_f32.md")
+    try:
+        s = open(p).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_hash:\s*([0-9a-f]+)", s)
+    b = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", s)
+    if not m or not b or m.group(1) != kernel_hash():
+        return None
+    return float(b.group(1))
+
+
+def run_gpu(args, rank, world, local):
+    import torch
+    import paper_1003_3779_gb300.qw as qw
+    from paper_1003_3779_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    hbm_gbs, sm_max_mhz, peak_src = load_peaks()
+    stream = torch.cuda.current_stream()
+
+    global N_SITES
+    N_SITES = args.n_sites
+    psi0 = inputs.random_state((2, N_SITES), seed=SEED, dtype=np.complex64)
+    dev0 = torch.from_numpy(psi0).to(f"cuda:{local}")
+    C = inputs.su2(THETA)
+    P_dev = torch.empty(N_SITES, dtype=torch.float32, device=f"cuda:{local}")
+
+    w = qw.Walk((N_SITES,), prec="f32")
+    w.set_coin(C)
+    w.set_state(dev0)
+    if args.plan:
+        pk, pt = (int(x) for x in args.plan.split(","))
+        w.set_plan(pk, pt)
+        tune = {"tuned": False, "plan": args.plan}
+    else:
+        tune = json.loads(w.autotune())
+    K, tile = w.plan()
+    desc = w.describe()
+    launches_step = math.ceil(T_STEPS / K)
+
+    def one_step(ev_a=None, ev_b=None):
+        qw.qw_set_state(w.h, dev0)
+        if ev_a is not None:
+            ev_a.record(stream)
+        qw.qw_step(w.h, T_STEPS)
+        if ev_b is not None:
+            ev_b.record(stream)
+        qw.qw_probabilities(w.h, P_dev, want_norm=False)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(dist, local)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for i in range(args.steps):
+            one_step(*evs[i])
+        stop.record(stream)
+        torch.cuda.synchronize()
+    barrier(dist, local)
+    elapsed = start.elapsed_time(stop) / 1e3
+    tmax = max_over_ranks(dist, elapsed, local)
+    step_kernel_s = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+    norm = qw.qw_probabilities(w.h, P_dev)
+    units = 2.0 * N_SITES * T_STEPS * args.steps
+    value = aggregate_throughput(units, tmax, world)
+
+    # roofline of the dominant kernel (the temporal-blocking step kernel)
+    avg_launch_s = step_kernel_s / (args.steps * launches_step)
+    k_eff = T_STEPS / launches_step                       # steps per launch (average)
+    if desc["coin_kind"] == "hadamard_class":
+        # 4 additions per site-step (a0 +- a1, re and im); one FP32 add per lane per clock
+        flops_site_step, flops_per_lane_clk, op = 4.0, 1, "FADD"
+    else:
+        # 8 FMAs per site-step (real 2x2 coin on complex amplitudes) = 16 flops
+        flops_site_step, flops_per_lane_clk, op = 16.0, 2, "FFMA"
+    flops_launch = flops_site_step * N_SITES * k_eff
+    bytes_launch = 32.0 * N_SITES                         # 2 planes x 8 B read + written
+    alu_peak = SMS * FP32_LANES * flops_per_lane_clk * sm_max_mhz * 1e6 / 1e12   # TFLOP/s
+    ach_tflops = flops_launch / avg_launch_s / 1e12
+    ach_gbs = bytes_launch / avg_launch_s / 1e9
+    alu_frac, hbm_frac = ach_tflops / alu_peak, ach_gbs / hbm_gbs
+    traffic = ncu_traffic()
+    if alu_frac >= hbm_frac:
+        roof = {"bound": "alu", "achieved": ach_tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": alu_frac, "traffic": traffic,
+                "peak_source": f"152 SMs x 128 FP32 lanes x {flops_per_lane_clk} flop ({op}) x "
+                               f"{sm_max_mhz:.0f} MHz (derived)",
+                "hbm_view": {"achieved_gbs": ach_gbs, "peak_gbs": hbm_gbs, "frac": hbm_frac,
+                             "peak_source": f"{peak_src} HBM copy"}}
+    else:
+        roof = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm_gbs, "unit": "GB/s",
+                "frac": hbm_frac, "traffic": traffic, "peak_source": f"{peak_src} HBM copy",
+                "alu_view": {"achieved_tflops": ach_tflops, "peak_tflops": alu_peak, "frac": alu_frac}}
+    roof.update({"kernel": "k_step1d<f32,R=%d,%s coin>" % (tile, desc["coin_kind"]), "k": K,
+                 "flops_per_site_step": flops_site_step,
+                 "avg_launch_ms": avg_launch_s * 1e3,
+                 "effective_bytes_per_site_step": bytes_launch / N_SITES / k_eff})
+
+    # k = 1 (one step per HBM round trip): the plain fused step against the HBM roof
+    w.set_plan(1, tile)
+    qw.qw_set_state(w.h, dev0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    qw.qw_step(w.h, 8)
+    e0.record(stream)
+    qw.qw_step(w.h, 64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    k1_s = e0.elapsed_time(e1) / 1e3 / 64
+    roof_k1 = {"bound": "hbm", "achieved": 32.0 * N_SITES / k1_s / 1e9, "peak": hbm_gbs,
+               "unit": "GB/s", "frac": 32.0 * N_SITES / k1_s / 1e9 / hbm_gbs,
+               "frac_of_8000": 32.0 * N_SITES / k1_s / 1e9 / 8000.0}
+    w.set_plan(K, tile)
+
+    # accuracy and the other precision forms on the same input (rank 0 only)
+    forms, accuracy = {}, {}
+    if rank == 0 and not args.skip_forms:
+        qw.qw_set_state(w.h, dev0)
+        qw.qw_step(w.h, T_STEPS)
+        P32 = torch.empty(N_SITES, dtype=torch.float64, device=f"cuda:{local}")
+        qw.qw_probabilities(w.h, P32)
+        ref = None
+        for name in ("f64", "bf16", "comp"):
+            wf = qw.Walk((N_SITES,), prec=name)
+            wf.set_coin(C)
+            wf.set_state(dev0)
+            wf.autotune()
+            Kf, tf = wf.plan()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            qw.qw_step(wf.h, T_STEPS)
+            b.record(stream)
+            Pf = torch.empty(N_SITES, dtype=torch.float64, device=f"cuda:{local}")
+            nf = qw.qw_probabilities(wf.h, Pf)
+            torch.cuda.synchronize()
+            ts = a.elapsed_time(b) / 1e3
+            forms[name] = {"value": 2.0 * N_SITES * T_STEPS / ts, "unit": UNIT, "k": Kf,
+                           "tile": tf, "norm": nf}
+            if name == "f64":
+                ref = Pf
+            else:
+                forms[name]["l1_vs_f64"] = float((Pf - ref).abs().sum())
+                forms[name]["maxabs_p_vs_f64"] = float((Pf - ref).abs().max())
+            del Pf
+            wf.close()
+        accuracy = {"l1_vs_f64_gpu": float((P32 - ref).abs().sum()),
+                    "maxabs_p_vs_f64_gpu": float((P32 - ref).abs().max()),
+                    "norm_f32": norm, "reference": "FP64 GPU path, same input, T=4096"}
+        forms["f32"] = {"value": value / world, "unit": UNIT, "k": K, "tile": tile,
+                        "l1_vs_f64": accuracy["l1_vs_f64_gpu"]}
+        del P32, ref
+
+    # end to end through the C ABI with host buffers (pinned), rank-local
+    e2e = None
+    if not args.skip_e2e:
+        host_in = torch.from_numpy(psi0).pin_memory()
+        host_P = torch.empty(N_SITES, dtype=torch.float32).pin_memory()
+        hin, hP = host_in.numpy(), host_P.numpy()
+        qw.qw_set_state(w.h, hin)
+        qw.qw_step(w.h, T_STEPS)
+        qw.qw_probabilities(w.h, hP)
+        n_e2e = max(1, min(args.steps, 3))
+        barrier(dist, local)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            qw.qw_set_state(w.h, hin)
+            qw.qw_step(w.h, T_STEPS)
+            qw.qw_probabilities(w.h, hP)
+        torch.cuda.synchronize()
+        te = max_over_ranks(dist, time.perf_counter() - t0, local)
+        e2e = {"value": aggregate_throughput(2.0 * N_SITES * T_STEPS * n_e2e, te, world),
+               "unit": UNIT, "h2d_bytes_per_step": int(hin.nbytes),
+               "d2h_bytes_per_step": int(hP.nbytes) + 8, "steps": n_e2e}
+        del host_in, host_P
+    w.close()
+    return {
+        "value": value, "elapsed": tmax, "norm": norm, "roofline": roof, "roofline_k1": roof_k1,
+        "forms": forms, "accuracy": accuracy, "e2e": e2e, "clocks": clk.summary(), "tune": tune,
+        "K": K, "tile": tile, "launches": args.steps * (launches_step + 2), "dist": dist,
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-forms", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--n-sites", type=int, default=N_SITES,
+                    help="cycle length (default 2^27; smaller only for profiling captures)")
+    ap.add_argument("--plan", default="", help="fixed 'k,tile' instead of the autotuner")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        t0 = time.perf_counter()
+        samples = [cpu_oracle_sample(target_s=max(4.0, 40.0 / max(1, args.steps + args.warmup)))
+                   for _ in range(args.warmup + args.steps)][args.warmup:]
+        vals = [s["value"] for s in samples]
+        v = statistics.median(vals)
+        total = time.perf_counter() - t0
+        cb = dict(samples[-1])
+        cb["value"] = v
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / (args.steps + args.warmup),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}))
+        return
+
+    r = run_gpu(args, rank, world, local)
+    if rank != 0:
+        return
+    cpu = None if args.skip_cpu else cpu_oracle_sample()
+    out = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * r["elapsed"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if N_SITES == 1 << 27 else f"{WORKLOAD} (N={N_SITES})",
+                   "sites": N_SITES, "coin_dim": 2, "T": T_STEPS,
+                   "k": r["K"], "tile": r["tile"], "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (2 GiB state, 129 MB L2); no flush needed",
+                   "step": "set_state (device copy) + T=4096 walk steps + marginals/norm"},
+        "clocks": r["clocks"], "e2e": r["e2e"], "gpu_launches": r["launches"],
+        "roofline": r["roofline"], "roofline_k1": r["roofline_k1"], "cpu_baseline": cpu,
+        "accuracy": r["accuracy"], "forms": r["forms"], "norm": r["norm"], "autotune": r["tune"],
+    }
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

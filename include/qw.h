@@ -1,0 +1,229 @@
+/*
+ * qw.h -- C ABI of the GB300 (sm_103a) discrete-time coined quantum-walk library.
+ *
+ * The operation is the one-step walk operator of Sawerwain & Gielerak,
+ * "GPGPU based simulations for one and two dimensional quantum walks"
+ * (arXiv:1003.3779):
+ *
+ *   U = S (I (x) C)                      (Sec. 2.1, restated as S (C (x) I) in Sec. 3)
+ *   C = (C_v)_v  unitary coin on the coin register of each site v   (Sec. 2.1)
+ *   S |v, e> = |v', e>  moves the walker along the edge its coin names (Sec. 2.1)
+ *
+ * on the lattice Z^1 (here the cycle Z_N, coin space C^2, Sec. 2.2) and Z^2
+ * (here the torus Z_Lx x Z_Ly, coin space C^4 = two coin qubits, Sec. 2.2 and
+ * the two-qubit state of Sec. 3).  Probabilities are the coin marginals
+ * P(v) = sum_c |psi(v,c)|^2, whose sum is the normalisation of Sec. 2.2.
+ *
+ * Conventions used by every call:
+ *   - coin basis / directions: 1D coin 0 moves x -> x-1, coin 1 moves x -> x+1;
+ *     2D coin 0: +x, 1: -x, 2: +y, 3: -y.  (The paper's own labelling of the
+ *     2D shift equation in Sec. 3 is a permutation of this basis.)
+ *   - moving shift:    S|v,c> = |v + e_c, c>;
+ *     flip-flop shift: S|v,c> = |v + e_c, c xor 1>.
+ *   - a closed link (broken link, Sec. 3 "RBL") reflects: the amplitude stays
+ *     on its site, in coin c xor 1 (moving) or c (flip-flop).
+ *   - state layout seen by callers: d coin-major planes of nsites complex
+ *     numbers, re/im interleaved; site index v = x (1D) or v = y*Lx + x (2D).
+ *     Inside the library the planes are padded; callers never see the padding.
+ *   - coins are row-major d x d complex matrices, re/im interleaved doubles;
+ *     C_v acts as phi(v)[r] = sum_c C_v[r][c] psi(v)[c].
+ *
+ * Ownership: a handle owns all of its device memory.  Pointers passed in are
+ * borrowed for the duration of the call only and are never freed by the
+ * library; device pointers may come from any allocator (e.g. torch tensors).
+ * Streams: every call is ordered on the handle's CUDA stream.  Calls that
+ * write to host memory or return a host scalar (norm, loss) synchronise the
+ * stream before returning; all others are asynchronous.
+ * Errors: every call returns a qw_status and never aborts or traps.  After an
+ * error the handle stays valid; qw_last_error() holds a message.  A CUDA
+ * error is reported as QW_ECUDA.  The state is never renormalised.
+ * Threads: a handle may be used by one host thread at a time.
+ */
+#ifndef QW_H
+#define QW_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qw_walk qw_walk;     /* opaque, library-owned */
+typedef struct qw_batch qw_batch;   /* opaque, library-owned */
+
+typedef enum {
+    QW_OK = 0,
+    QW_EINVAL = 1,        /* bad argument (null pointer, size, enum value) */
+    QW_ENOMEM = 2,        /* device or host allocation failed */
+    QW_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    QW_ESTATE = 4,        /* call not valid in the handle's current state */
+    QW_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    QW_EUNSUPPORTED = 6   /* valid request this build does not implement */
+} qw_status;
+
+typedef enum {
+    QW_BC_PERIODIC = 0,   /* cycle / torus */
+    QW_BC_SEGMENT = 1,    /* finite segment: the links across the edge are closed (Sec. 3, Fig. 2 "segment") */
+    QW_BC_LINE = 2        /* finite window of the infinite line: amplitude crossing the edge is dropped (Sec. 3 "line") */
+} qw_boundary;
+
+typedef enum { QW_SHIFT_MOVING = 0, QW_SHIFT_FLIPFLOP = 1 } qw_shift;
+
+/* Storage / arithmetic of the state.  QW_F64: double storage and arithmetic.
+ * QW_F32: float.  QW_F32_BF16STORE: bfloat16 storage, float arithmetic (one
+ * rounding to bf16 per HBM round trip).  QW_F32_COMP: each amplitude is an
+ * unevaluated float pair hi+lo, arithmetic in double-float (TwoSum /
+ * TwoProduct), about 44 significant bits. */
+typedef enum { QW_F64 = 0, QW_F32 = 1, QW_F32_BF16STORE = 2, QW_F32_COMP = 3 } qw_precision;
+
+/* Element type of caller-side state buffers. */
+typedef enum { QW_C128 = 0, QW_C64 = 1 } qw_cdtype;
+/* Element type of caller-side real buffers (probabilities). */
+typedef enum { QW_R64 = 0, QW_R32 = 1 } qw_rdtype;
+
+/* ---------------------------------------------------------------- walks */
+
+/* Create a walk on the cycle (ndim=1, dims[0]=N, coin_dim=2) or the torus
+ * (ndim=2, dims={Lx, Ly}, coin_dim=4), Sec. 2.2.  cuda_stream: a cudaStream_t
+ * (NULL = legacy default stream).  The coin starts as the identity, the state
+ * as all zeros.  Allocates two state buffers on the current device.
+ * QW_EINVAL for ndim not 1/2, coin_dim != 2*ndim, a dimension < 1, or an
+ * unknown enum; QW_ENOMEM if the device allocation fails. */
+qw_status qw_create(int ndim, const int64_t *dims, int coin_dim, qw_boundary bc,
+                    qw_shift shift, qw_precision prec, void *cuda_stream,
+                    qw_walk **out);
+
+/* Release every resource of the handle (NULL is accepted). */
+qw_status qw_destroy(qw_walk *w);
+
+/* Coin flip transformation (Sec. 2.1).  per_site = 0: `coin` holds one d x d
+ * matrix (2*d*d doubles); per_site = 1: nsites matrices, site-major.
+ * on_device selects whether `coin` is a host or device pointer.  Unitarity is
+ * the caller's responsibility (the walk is linear either way). */
+qw_status qw_set_coin(qw_walk *w, const double *coin, int per_site, int on_device);
+
+/* Per-site phase coin C_v = base . diag(e^{i phi_{v,k}}) (the phase acts
+ * first).  base: one d x d matrix (host doubles, 2*d*d).  phi: nsites*d reals,
+ * site-major (phi[v*d + k]), float, host or device (on_device).  The phases are
+ * copied; later changes to the caller's buffer have no effect. */
+qw_status qw_set_coin_phases(qw_walk *w, const double *base, const float *phi, int on_device);
+
+/* Broken links (Sec. 3, RBL).  closed: ndim*nsites bytes, nonzero = closed;
+ * bytes [0, nsites) are the links from (x,y) to (x+1,y), bytes
+ * [nsites, 2 nsites) (2D only) the links from (x,y) to (x,y+1).  NULL clears
+ * all.  Host or device (on_device). */
+qw_status qw_set_links(qw_walk *w, const uint8_t *closed, int on_device);
+
+/* Replace the state: amp holds d coin-major planes of nsites complex numbers
+ * of type dtype (host or device).  Converted to the walk's precision on the
+ * device (QW_F32_COMP keeps the rounding residue of a QW_C128 input). */
+qw_status qw_set_state(qw_walk *w, const void *amp, qw_cdtype dtype, int on_device);
+
+/* Copy the state out in the same layout (converted to dtype). */
+qw_status qw_get_state(qw_walk *w, void *amp_out, qw_cdtype dtype, int on_device);
+
+/* Apply U^T (T >= 0; T = 0 does nothing).  Runs ceil(T/k) fused kernels, each
+ * advancing k steps per HBM round trip (temporal blocking), k from the plan. */
+qw_status qw_step(qw_walk *w, int64_t T);
+
+/* Apply (U^dagger)^T: the walk run backward. */
+qw_status qw_step_adjoint(qw_walk *w, int64_t T);
+
+/* Coin marginals P(v) = sum_c |psi(v,c)|^2 into P_out (nsites values of type
+ * pdtype, host or device; may be NULL) and the total norm sum_v P(v),
+ * accumulated in double in a fixed order (bitwise reproducible), into
+ * *norm_out (host; may be NULL).  Synchronises when norm_out is given or
+ * P_out is a host pointer. */
+qw_status qw_probabilities(qw_walk *w, void *P_out, qw_rdtype pdtype, int on_device,
+                           double *norm_out);
+
+/* Execution plan of qw_step: temporal depth k (steps per kernel, >= 1) and
+ * tile (sites per thread in 1D, 0 = library default).  k = 0 restores the
+ * default / tuned plan.  QW_EINVAL for a combination the kernels reject. */
+qw_status qw_set_plan(qw_walk *w, int depth_k, int tile);
+qw_status qw_get_plan(const qw_walk *w, int *depth_k, int *tile);
+
+/* Time the candidate plans on this walk (CUDA events on the walk's stream,
+ * reading the current state, writing only the scratch buffer, so the state is
+ * unchanged) and keep the fastest.  Results are cached per (lattice shape,
+ * precision, coin kind) in memory and, if the environment variable
+ * QW_TUNE_CACHE names a file, in that JSON file.  report (may be NULL)
+ * receives a one-line JSON summary, truncated to report_len bytes. */
+qw_status qw_autotune(qw_walk *w, char *report, size_t report_len);
+
+/* One-line JSON description of the handle: lattice, precision, the coin kind
+ * the kernels specialise on ("real", "complex", "grover", "hadamard2",
+ * "per_site", "phase", "hadamard_class"), the plan (k, tile), which kernel
+ * family runs the step and the bytes of one state buffer.  Truncated to len. */
+qw_status qw_describe(const qw_walk *w, char *buf, size_t len);
+
+/* Number of sites (N or Lx*Ly). */
+int64_t qw_nsites(const qw_walk *w);
+
+/* Wait for all work queued on the walk's stream. */
+qw_status qw_synchronize(qw_walk *w);
+
+/* Gradient of the region mass L = sum_{v in rect, c} |psi_T(v,c)|^2 with
+ * respect to the per-site coin phases phi_{v,k} set by qw_set_coin_phases
+ * (2D torus only), starting from the current state.  rect = {x0, y0, w, h}:
+ * x0 <= x < x0+w, y0 <= y < y0+h, inside the lattice.  Runs T forward steps
+ * storing psi every K steps (checkpoints), then walks back with U^dagger,
+ * re-seeding psi from the checkpoint at each segment boundary so FP32 drift
+ * is bounded by K steps, and accumulates
+ *     dL/dphi_{v,k} = sum_t -2 Im( conj(a_t(v)_k) (D_v psi_t(v))_k ),
+ *     a_t = B^dagger S^dagger lambda_{t+1},  lambda_T = 1_rect psi_T,
+ * in double.  grad_phi: nsites*d doubles, site-major (host or device).
+ * *loss_out (host, may be NULL) receives L.  The walk's state is left at psi_T.
+ * QW_ESTATE if no phase coin is set. */
+qw_status qw_backward(qw_walk *w, const int64_t rect[4], int64_t T, int64_t K,
+                      double *loss_out, double *grad_phi, int on_device);
+
+/* ---------------------------------------------------------------- batches */
+
+/* A batch of independent 1D walks on cycles (Sec. 2.2), walk i with N[i]
+ * sites, T[i] steps, its own 2x2 coin (coins + 8*i: row-major complex), and the
+ * localised initial state |x0[i]> (x) (coin_state[0]|0> + coin_state[1]|1>)
+ * (coin_state: 2 complex = 4 doubles).  prec: QW_F32 or QW_F32_BF16STORE
+ * (state storage; arithmetic is float).  All arrays are host pointers.
+ * Device memory: the final states of all walks and their probabilities. */
+qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T,
+                          const double *coins, const int64_t *x0,
+                          const double *coin_state, qw_precision prec,
+                          void *cuda_stream, qw_batch **out);
+
+/* Run every walk of the batch from its initial state for its own T[i] steps
+ * (one persistent kernel launch, replayed from a CUDA graph after the first
+ * call) and compute each walk's probabilities.  Repeated calls start again
+ * from the initial states. */
+qw_status qw_batch_step(qw_batch *b);
+
+/* Probabilities of all walks, concatenated in walk order (walk i starts at
+ * sum_{j<i} N[j]), float, host or device; norms (host, may be NULL): nwalks
+ * doubles, the sum of each walk's P.  Synchronises. */
+qw_status qw_batch_probabilities(qw_batch *b, float *P_concat, int on_device, double *norms);
+
+/* Final state of walk i (2 planes of N[i] complex, dtype, host pointer). */
+qw_status qw_batch_get_state(qw_batch *b, int walk, void *amp_out, qw_cdtype dtype);
+
+qw_status qw_batch_destroy(qw_batch *b);
+
+/* ---------------------------------------------------------------- misc */
+
+const char *qw_status_string(qw_status s);
+const char *qw_last_error(const qw_walk *w);
+const char *qw_batch_last_error(const qw_batch *b);
+/* Version string of the library ("qw <major>.<minor> sm_103a"). */
+const char *qw_version(void);
+
+/* Bounded-wait self test: launches one kernel that waits on a device flag that
+ * nothing sets, giving up after `spins` polls; returns QW_ETIMEOUT when the
+ * wait gave up (the expected outcome) and leaves the context usable.  Exists
+ * so failure detection can be tested without hanging a GPU. */
+qw_status qw_debug_bounded_wait(int64_t spins, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QW_H */

@@ -1,0 +1,213 @@
+// k_step1d.cuh -- fused coin + shift on the cycle Z_N with temporal blocking.
+//
+// One step is U = S (I (x) C) (Sec. 2.1) on the 1D walk of Sec. 2.2: coin 0 moves
+// x -> x-1, coin 1 moves x -> x+1 (moving shift) or the same moves with the
+// coin flipped (flip-flop).  The paper's kernel (Sec. 3, figure "one iteration
+// segment") does one step per launch, one thread per site, reading both coin
+// planes from global memory.  Here each warp owns a tile of 32*R consecutive
+// sites held in registers (R per lane), applies K steps back to back, moving
+// the one value per plane that crosses a lane boundary with a warp shuffle,
+// and writes only the 32R - 2K central sites: the light cone of a site after
+// K steps is +-K sites, so those outputs never saw the tile edge.  Tiles of
+// neighbouring warps overlap by 2K sites (recomputed redundantly), which is
+// what lets warps run with no synchronisation at all.  HBM traffic per step
+// is (2 planes read + 2 written) / K per site.
+//
+// The same kernel, with ADJ=1, applies U^dagger = (I (x) C^dagger) S^dagger.
+//
+// Per-plane factors: `pre` after the load, `post` before the store.  They carry
+// the signs and the scale lambda^K of the Hadamard-class coin (CK_SIGN_*), and
+// for other global coins the compensation of the one systematic error of a
+// rounded coin: with C_f the coin rounded to the compute precision,
+// C_f^dagger C_f = alpha^2 I (exactly for rotation / Hadamard-type coins, to
+// first order otherwise), so K steps scale the norm by alpha^K and the host
+// passes post = alpha^-K.  Without it 1/sqrt2 rounded to float shrinks the norm
+// by 3.6e-8 per step (1.5e-4 after 4096 steps).
+#pragma once
+#include "qw_internal.cuh"
+
+namespace qw {
+
+__device__ __forceinline__ int64_t wrap_index(int64_t g, int64_t n) {
+    int64_t r = g % n;
+    return r < 0 ? r + n : r;
+}
+
+// Load R consecutive sites starting at global site s (periodic wrap), one plane.
+template <int P, int R>
+__device__ __forceinline__ void load_run(View v, int c, int64_t s, int64_t n,
+                                         Cx<typename St<P>::real> (&o)[R]) {
+    using S = St<P>;
+    if (s >= 0 && s + R <= n && (s % S::VEC) == 0) {
+#pragma unroll
+        for (int j = 0; j < R; j += S::VEC) S::ldv(v, c, s + j, &o[j]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < R; ++j) o[j] = S::ld(v, c, wrap_index(s + j, n));
+    }
+}
+
+// Store the lane's R sites (global s .. s+R-1, tile positions j0 .. j0+R-1),
+// keeping only tile positions in [lo, hi).
+template <int P, int R>
+__device__ __forceinline__ void store_run(View v, int c, int64_t s, int j0, int lo, int hi,
+                                          const Cx<typename St<P>::real> (&a)[R]) {
+    using S = St<P>;
+    if (j0 >= lo && j0 + R <= hi && (s % S::VEC) == 0) {
+#pragma unroll
+        for (int j = 0; j < R; j += S::VEC) S::stv(v, c, s + j, &a[j]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            if (j0 + j >= lo && j0 + j < hi) S::st(v, c, s + j, a[j]);
+    }
+}
+
+// phi = C psi for one site, d = 2.
+template <int CK, class R>
+__device__ __forceinline__ void coin2(const CoinP<R> &cp, const Cx<R> *m, Cx<R> a0, Cx<R> a1,
+                                      Cx<R> &p0, Cx<R> &p1) {
+    if (CK == CK_REAL) {
+        p0 = rfma(cp.re[1], a1, rmul(cp.re[0], a0));
+        p1 = rfma(cp.re[3], a1, rmul(cp.re[2], a0));
+    } else if (CK == CK_COMPLEX) {
+        Cx<R> c00{cp.re[0], cp.im[0]}, c01{cp.re[1], cp.im[1]};
+        Cx<R> c10{cp.re[2], cp.im[2]}, c11{cp.re[3], cp.im[3]};
+        p0 = cfma(c01, a1, cmul(c00, a0));
+        p1 = cfma(c11, a1, cmul(c10, a0));
+    } else if (CK == CK_SIGN_P) {
+        p0 = cadd(a0, a1);
+        p1 = csub(a0, a1);
+    } else if (CK == CK_SIGN_M) {
+        p0 = csub(a0, a1);
+        p1 = cadd(a0, a1);
+    } else {  // CK_PERSITE: m points at this site's 4 entries
+        p0 = cfma(m[1], a1, cmul(m[0], a0));
+        p1 = cfma(m[3], a1, cmul(m[2], a0));
+    }
+}
+
+// psi = C^dagger b for one site, d = 2.
+template <int CK, class R>
+__device__ __forceinline__ void coin2_adj(const CoinP<R> &cp, const Cx<R> *m, Cx<R> b0, Cx<R> b1,
+                                          Cx<R> &a0, Cx<R> &a1) {
+    if (CK == CK_REAL) {
+        a0 = rfma(cp.re[2], b1, rmul(cp.re[0], b0));
+        a1 = rfma(cp.re[3], b1, rmul(cp.re[1], b0));
+    } else if (CK == CK_COMPLEX) {
+        Cx<R> c00{cp.re[0], cp.im[0]}, c01{cp.re[1], cp.im[1]};
+        Cx<R> c10{cp.re[2], cp.im[2]}, c11{cp.re[3], cp.im[3]};
+        a0 = cadd(conjmul(c00, b0), conjmul(c10, b1));
+        a1 = cadd(conjmul(c01, b0), conjmul(c11, b1));
+    } else if (CK == CK_SIGN_P || CK == CK_SIGN_M) {
+        // (U^dagger)^K = lambda^K a^{K-1} diag(1, s) [H_sigma S^dagger]^K diag(a, sigma c):
+        // the same addition pattern, applied after the pull
+        coin2<CK>(cp, m, b0, b1, a0, a1);
+    } else {
+        a0 = cadd(conjmul(m[0], b0), conjmul(m[2], b1));
+        a1 = cadd(conjmul(m[1], b0), conjmul(m[3], b1));
+    }
+}
+
+// W = 32R - 2K output sites per warp; nwarps = ceil(n / W).
+template <int P, int R, int CK, int FF, int ADJ>
+__global__ void __launch_bounds__(128)
+k_step1d(View in, View out, int64_t n, int K, int64_t W, int64_t nwarps,
+         CoinP<typename St<P>::real> cp, const Cx<typename St<P>::real> *__restrict__ coins,
+         typename St<P>::real pre0, typename St<P>::real pre1,
+         typename St<P>::real post0, typename St<P>::real post1) {
+    using real = typename St<P>::real;
+    using C = Cx<real>;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (warp >= nwarps) return;  // uniform per warp
+    const int64_t out0 = warp * W;
+    const int wthis = (int)min(W, n - out0);
+    const int j0 = lane * R;
+    const int64_t s = out0 - K + j0;
+
+    C a0[R], a1[R];
+    load_run<P, R>(in, 0, s, n, a0);
+    load_run<P, R>(in, 1, s, n, a1);
+    if (!is_one(pre0)) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) a0[i] = rmul(pre0, a0[i]);
+    }
+    if (!is_one(pre1)) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) a1[i] = rmul(pre1, a1[i]);
+    }
+
+    // per-site coins stay with their site while the amplitudes move through
+    constexpr int NM = (CK == CK_PERSITE) ? 4 * R : 1;
+    C m[NM];
+    if (CK == CK_PERSITE) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            int64_t g = wrap_index(s + i, n);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) m[4 * i + e] = coins[4 * g + e];
+        }
+    }
+
+    // unrolled by two so the register shift of one step is a renaming into the
+    // other step's registers instead of moves at the loop back edge
+#pragma unroll 2
+    for (int t = 0; t < K; ++t) {
+        if (!ADJ) {
+            C p0[R], p1[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) coin2<CK>(cp, &m[(CK == CK_PERSITE) ? 4 * i : 0], a0[i], a1[i], p0[i], p1[i]);
+            // coin 0 arrives from the right neighbour site, coin 1 from the left
+            C from_right = shfl_down(p0[0], 1);
+            C from_left = shfl_up(p1[R - 1], 1);
+            if (!FF) {
+#pragma unroll
+                for (int i = 0; i < R - 1; ++i) a0[i] = p0[i + 1];
+                a0[R - 1] = from_right;
+#pragma unroll
+                for (int i = R - 1; i > 0; --i) a1[i] = p1[i - 1];
+                a1[0] = from_left;
+            } else {
+#pragma unroll
+                for (int i = 0; i < R - 1; ++i) a1[i] = p0[i + 1];
+                a1[R - 1] = from_right;
+#pragma unroll
+                for (int i = R - 1; i > 0; --i) a0[i] = p1[i - 1];
+                a0[0] = from_left;
+            }
+        } else {
+            // S^dagger: moving  b0(x) = psi0(x-1), b1(x) = psi1(x+1);
+            //           flip-flop b0(x) = psi1(x-1), b1(x) = psi0(x+1)
+            C lsrc[R], rsrc[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                lsrc[i] = FF ? a1[i] : a0[i];
+                rsrc[i] = FF ? a0[i] : a1[i];
+            }
+            C from_left = shfl_up(lsrc[R - 1], 1);
+            C from_right = shfl_down(rsrc[0], 1);
+            C b0[R], b1[R];
+#pragma unroll
+            for (int i = R - 1; i > 0; --i) b0[i] = lsrc[i - 1];
+            b0[0] = from_left;
+#pragma unroll
+            for (int i = 0; i < R - 1; ++i) b1[i] = rsrc[i + 1];
+            b1[R - 1] = from_right;
+#pragma unroll
+            for (int i = 0; i < R; ++i) coin2_adj<CK>(cp, &m[(CK == CK_PERSITE) ? 4 * i : 0], b0[i], b1[i], a0[i], a1[i]);
+        }
+    }
+    if (!is_one(post0)) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) a0[i] = rmul(post0, a0[i]);
+    }
+    if (!is_one(post1)) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) a1[i] = rmul(post1, a1[i]);
+    }
+    store_run<P, R>(out, 0, s, j0, K, K + wthis, a0);
+    store_run<P, R>(out, 1, s, j0, K, K + wthis, a1);
+}
+
+}  // namespace qw

@@ -1,0 +1,158 @@
+// launch_step.cuh -- host-side launch of the step kernels for one precision.
+// Included once per precision by step_<prec>.cu so the template instances of
+// each precision compile in their own translation unit (in parallel).
+#pragma once
+#include "qw_internal.cuh"
+#include "k_step1d.cuh"
+#include "k_step2d.cuh"
+#include "k_generic.cuh"
+
+namespace qw {
+
+// Sites per lane compiled for the 1D kernel: two forward tiles, and the
+// default tile used by the per-site coin and the adjoint.
+template <int P> struct Tiles1D;
+template <> struct Tiles1D<P_F32> { static constexpr int A = 8, B = 16, DEF = 16; };
+template <> struct Tiles1D<P_BF16> { static constexpr int A = 8, B = 16, DEF = 16; };
+template <> struct Tiles1D<P_F64> { static constexpr int A = 4, B = 8, DEF = 8; };
+template <> struct Tiles1D<P_COMP> { static constexpr int A = 4, B = 8, DEF = 4; };
+
+// Sites per lane of the 2D kernel (32 bytes of one plane per lane).
+template <int P> struct Tile2D { static constexpr int R = 32 / St<P>::SLOT_BYTES < 1 ? 1 : 32 / St<P>::SLOT_BYTES; };
+template <> struct Tile2D<P_COMP> { static constexpr int R = 4; };
+
+template <int P, int R, int CK, int FF, int ADJ>
+static void go1d(const Step1DArgs &a, const CoinP<typename St<P>::real> &cp, cudaStream_t s) {
+    const int64_t W = 32LL * R - 2LL * a.K;
+    const int64_t nwarps = (a.n + W - 1) / W;
+    const int64_t blocks = (nwarps + 3) / 4;
+    k_step1d<P, R, CK, FF, ADJ><<<(unsigned)blocks, 128, 0, s>>>(
+        a.in, a.out, a.n, a.K, W, nwarps, cp,
+        static_cast<const Cx<typename St<P>::real> *>(a.coins),
+        real_from_double<typename St<P>::real>(a.pre0), real_from_double<typename St<P>::real>(a.pre1),
+        real_from_double<typename St<P>::real>(a.post0), real_from_double<typename St<P>::real>(a.post1));
+}
+
+template <int P, int R, int ADJ>
+static bool go1d_kind(const Step1DArgs &a, const CoinP<typename St<P>::real> &cp, cudaStream_t s) {
+    const bool ff = a.shift == QW_SHIFT_FLIPFLOP;
+    switch (a.kind) {
+        case CK_REAL: ff ? go1d<P, R, CK_REAL, 1, ADJ>(a, cp, s) : go1d<P, R, CK_REAL, 0, ADJ>(a, cp, s); return true;
+        case CK_COMPLEX: ff ? go1d<P, R, CK_COMPLEX, 1, ADJ>(a, cp, s) : go1d<P, R, CK_COMPLEX, 0, ADJ>(a, cp, s); return true;
+        case CK_SIGN_P: if (ff) return false; go1d<P, R, CK_SIGN_P, 0, ADJ>(a, cp, s); return true;
+        case CK_SIGN_M: if (ff) return false; go1d<P, R, CK_SIGN_M, 0, ADJ>(a, cp, s); return true;
+        default: return false;
+    }
+}
+
+// Largest K the 1D kernel accepts for tile R: at least half the tile is output.
+inline int max_k_1d(int R) { return 8 * R; }
+
+template <int P>
+int tile1d_effective(int tile, int kind, int adj) {
+    using T = Tiles1D<P>;
+    if (adj || kind == CK_PERSITE) return T::DEF;
+    return (tile == T::A || tile == T::B) ? tile : T::DEF;
+}
+
+template <int P>
+cudaError_t step1d_t(const Step1DArgs &a0, const void *coinp, int adj, cudaStream_t s) {
+    using T = Tiles1D<P>;
+    const auto &cp = *static_cast<const CoinP<typename St<P>::real> *>(coinp);
+    Step1DArgs a = a0;
+    a.tile = tile1d_effective<P>(a.tile, a.kind, adj);
+    if (a.K < 1 || a.K > max_k_1d(a.tile)) return cudaErrorInvalidValue;
+    const bool ff = a.shift == QW_SHIFT_FLIPFLOP;
+    if (!adj) {
+        if (a.kind == CK_PERSITE) {
+            ff ? go1d<P, T::DEF, CK_PERSITE, 1, 0>(a, cp, s) : go1d<P, T::DEF, CK_PERSITE, 0, 0>(a, cp, s);
+        } else if (a.tile == T::A) {
+            if (!go1d_kind<P, T::A, 0>(a, cp, s)) return cudaErrorInvalidValue;
+        } else {
+            if (!go1d_kind<P, T::B, 0>(a, cp, s)) return cudaErrorInvalidValue;
+        }
+    } else {
+        if (a.kind == CK_PERSITE) {
+            ff ? go1d<P, T::DEF, CK_PERSITE, 1, 1>(a, cp, s) : go1d<P, T::DEF, CK_PERSITE, 0, 1>(a, cp, s);
+        } else if (!go1d_kind<P, T::DEF, 1>(a, cp, s)) {
+            return cudaErrorInvalidValue;
+        }
+    }
+    return cudaGetLastError();
+}
+
+template <int P, int CK, int FF, int ADJ>
+static void go2d(const Step2DArgs &a, const CoinP<typename St<P>::real> &cp, cudaStream_t s) {
+    constexpr int R = Tile2D<P>::R;
+    const int64_t segs = (a.nx + 32 * R - 1) / (32 * R);
+    const int64_t nwarps = segs * a.ny;
+    const int64_t blocks = (nwarps + 3) / 4;
+    k_step2d<P, R, CK, FF, ADJ><<<(unsigned)blocks, 128, 0, s>>>(
+        a.in, a.out, a.nx, a.ny, segs, nwarps, cp, a.phi,
+        static_cast<const Cx<typename St<P>::real> *>(a.coins),
+        real_from_double<typename St<P>::real>(a.gain));
+}
+
+template <int P, int CK>
+static void go2d_ff(const Step2DArgs &a, const CoinP<typename St<P>::real> &cp, int adj, cudaStream_t s) {
+    const bool ff = a.shift == QW_SHIFT_FLIPFLOP;
+    if (!adj) ff ? go2d<P, CK, 1, 0>(a, cp, s) : go2d<P, CK, 0, 0>(a, cp, s);
+    else ff ? go2d<P, CK, 1, 1>(a, cp, s) : go2d<P, CK, 0, 1>(a, cp, s);
+}
+
+// Does the fast 2D kernel of precision P handle this coin kind?
+template <int P>
+constexpr bool fast2d_has_phase() { return P == P_F32 || P == P_F64; }
+
+template <int P>
+cudaError_t step2d_t(const Step2DArgs &a, const void *coinp, int adj, cudaStream_t s) {
+    const auto &cp = *static_cast<const CoinP<typename St<P>::real> *>(coinp);
+    switch (a.kind) {
+        case CK_REAL: go2d_ff<P, CK_REAL>(a, cp, adj, s); break;
+        case CK_COMPLEX: go2d_ff<P, CK_COMPLEX>(a, cp, adj, s); break;
+        case CK_GROVER: go2d_ff<P, CK_GROVER>(a, cp, adj, s); break;
+        case CK_HH: go2d_ff<P, CK_HH>(a, cp, adj, s); break;
+        case CK_PHASE:
+            if constexpr (fast2d_has_phase<P>()) { go2d_ff<P, CK_PHASE>(a, cp, adj, s); break; }
+            return cudaErrorNotSupported;
+        default: return cudaErrorNotSupported;
+    }
+    return cudaGetLastError();
+}
+
+template <int P, int CK>
+static void gogen(const StepGenericArgs &a, const CoinP<typename St<P>::real> &cp, cudaStream_t s) {
+    GenGeom g{a.ndim, a.nx, a.ny, a.nx * a.ny, a.shift, a.bc, a.links};
+    const int64_t blocks = (g.ns + 127) / 128;
+    k_step_generic<P, CK><<<(unsigned)blocks, 128, 0, s>>>(
+        a.in, a.out, g, a.adjoint, cp, static_cast<const Cx<typename St<P>::real> *>(a.coins), a.phi,
+        real_from_double<typename St<P>::real>(a.gain));
+}
+
+template <int P>
+cudaError_t generic_t(const StepGenericArgs &a, const void *coinp, cudaStream_t s) {
+    const auto &cp = *static_cast<const CoinP<typename St<P>::real> *>(coinp);
+    switch (a.kind) {
+        case CK_PERSITE: gogen<P, CK_PERSITE>(a, cp, s); break;
+        case CK_PHASE: gogen<P, CK_PHASE>(a, cp, s); break;
+        default: gogen<P, CK_COMPLEX>(a, cp, s); break;  // every global coin as a full matrix
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace qw
+
+// One translation unit per precision defines these three entry points.
+#define QW_DEFINE_STEP_LAUNCHERS(PREC, SUFFIX)                                                          \
+    namespace qw {                                                                                      \
+    cudaError_t launch_step1d_##SUFFIX(const Step1DArgs &a, const void *cp, int adj, cudaStream_t s) {  \
+        return step1d_t<PREC>(a, cp, adj, s);                                                           \
+    }                                                                                                   \
+    cudaError_t launch_step2d_##SUFFIX(const Step2DArgs &a, const void *cp, int adj, cudaStream_t s) {  \
+        return step2d_t<PREC>(a, cp, adj, s);                                                           \
+    }                                                                                                   \
+    cudaError_t launch_generic_##SUFFIX(const StepGenericArgs &a, const void *cp, cudaStream_t s) {     \
+        return generic_t<PREC>(a, cp, s);                                                               \
+    }                                                                                                   \
+    int tile1d_##SUFFIX(int tile, int kind, int adj) { return tile1d_effective<PREC>(tile, kind, adj); } \
+    }

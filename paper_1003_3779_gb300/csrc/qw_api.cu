@@ -1,0 +1,794 @@
+// qw_api.cu -- the C ABI of include/qw.h for single walks: handles, state and
+// coin set-up, the step loop, marginals, plans and the autotuner.
+//
+// A walk is the one-step operator U = S (I (x) C) of Sec. 2.1 applied to the
+// Z^1 / Z^2 walker states of Sec. 2.2-3 (cycle and torus, periodic, or the
+// finite segment / line of Sec. 3 with broken links).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "qw_handle.h"
+
+using namespace qw;
+
+// ------------------------------------------------------------------ helpers
+namespace qw {
+
+qw_status set_error(qw_walk *w, qw_status st, const std::string &msg) {
+    if (w) w->err = msg;
+    return st;
+}
+
+qw_status cuda_error(qw_walk *w, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    (void)cudaGetLastError();  // clear a non-sticky error so the handle stays usable
+    return set_error(w, e == cudaErrorMemoryAllocation ? QW_ENOMEM : QW_ECUDA, m);
+}
+
+bool fault_injected(const char *what) {
+    const char *f = std::getenv("QW_FAULT");
+    return f && std::strstr(f, what);
+}
+
+cudaError_t dev_alloc(void **p, size_t bytes) {
+    *p = nullptr;
+    if (fault_injected("alloc")) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
+static int slot_bytes_of(int prec) {
+    switch (prec) {
+        case QW_F64: return 16;
+        case QW_F32: return 8;
+        case QW_F32_BF16STORE: return 4;
+        case QW_F32_COMP: return 8;
+    }
+    return 0;
+}
+
+static size_t real_bytes(int prec) {  // bytes of one compute-precision real
+    return prec == QW_F64 ? 8 : (prec == QW_F32_COMP ? 8 : 4);
+}
+
+static cudaError_t step1d(int prec, const Step1DArgs &a, const void *cp, int adj, cudaStream_t s) {
+    switch (prec) {
+        case QW_F64: return launch_step1d_f64(a, cp, adj, s);
+        case QW_F32: return launch_step1d_f32(a, cp, adj, s);
+        case QW_F32_BF16STORE: return launch_step1d_bf16(a, cp, adj, s);
+        case QW_F32_COMP: return launch_step1d_comp(a, cp, adj, s);
+    }
+    return cudaErrorInvalidValue;
+}
+static cudaError_t step2d(int prec, const Step2DArgs &a, const void *cp, int adj, cudaStream_t s) {
+    switch (prec) {
+        case QW_F64: return launch_step2d_f64(a, cp, adj, s);
+        case QW_F32: return launch_step2d_f32(a, cp, adj, s);
+        case QW_F32_BF16STORE: return launch_step2d_bf16(a, cp, adj, s);
+        case QW_F32_COMP: return launch_step2d_comp(a, cp, adj, s);
+    }
+    return cudaErrorInvalidValue;
+}
+static cudaError_t stepgen(int prec, const StepGenericArgs &a, const void *cp, cudaStream_t s) {
+    switch (prec) {
+        case QW_F64: return launch_generic_f64(a, cp, s);
+        case QW_F32: return launch_generic_f32(a, cp, s);
+        case QW_F32_BF16STORE: return launch_generic_bf16(a, cp, s);
+        case QW_F32_COMP: return launch_generic_comp(a, cp, s);
+    }
+    return cudaErrorInvalidValue;
+}
+static int tile1d(int prec, int tile, int kind, int adj) {
+    switch (prec) {
+        case QW_F64: return tile1d_f64(tile, kind, adj);
+        case QW_F32: return tile1d_f32(tile, kind, adj);
+        case QW_F32_BF16STORE: return tile1d_bf16(tile, kind, adj);
+        case QW_F32_COMP: return tile1d_comp(tile, kind, adj);
+    }
+    return 0;
+}
+// tiles compiled for the forward 1D kernel, per precision
+static void tiles_of(int prec, int &a, int &b) {
+    if (prec == QW_F64 || prec == QW_F32_COMP) { a = 4; b = 8; }
+    else { a = 8; b = 16; }
+}
+
+static void default_plan(const qw_walk *w, int &k, int &tile) {
+    if (w->ndim == 2) { k = 1; tile = 0; return; }
+    switch (w->prec) {
+        case QW_F64: tile = 8; k = 8; break;
+        case QW_F32_COMP: tile = 4; k = 8; break;
+        default: tile = 16; k = 32; break;
+    }
+}
+
+static void effective_plan(const qw_walk *w, int &k, int &tile) {
+    default_plan(w, k, tile);
+    if (w->plan_k > 0) { k = w->plan_k; tile = w->plan_tile ? w->plan_tile : tile; }
+}
+
+// Global coin: store, classify, and convert to the compute precision.
+static void apply_global_coin(qw_walk *w, const double *h) {
+    const int d = w->d, n = d * d;
+    std::memcpy(w->coin_host, h, sizeof(double) * 2 * n);
+    bool real = true;
+    for (int i = 0; i < n; ++i) real = real && h[2 * i + 1] == 0.0;
+    int kind = real ? CK_REAL : CK_COMPLEX;
+    if (d == 4 && real) {
+        bool grover = true, hh = true;
+        for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) {
+                const double g = (r == c) ? -0.5 : 0.5;
+                const int sgn = ((r & c & 1) ^ ((r >> 1) & (c >> 1) & 1)) ? -1 : 1;  // H(x)H, c = 2j+k
+                grover = grover && std::fabs(h[2 * (4 * r + c)] - g) <= 1e-15;
+                hh = hh && std::fabs(h[2 * (4 * r + c)] - 0.5 * sgn) <= 1e-15;
+            }
+        if (grover) kind = CK_GROVER;
+        else if (hh) kind = CK_HH;
+    }
+    w->kind = kind;
+    std::memset(w->coinp, 0, sizeof(w->coinp));
+    double fro = 0.0;   // |C_f|_F^2 of the coin as the kernels see it
+    if (w->prec == QW_F64) {
+        auto *cp = reinterpret_cast<CoinP<double> *>(w->coinp);
+        for (int i = 0; i < n; ++i) { cp->re[i] = h[2 * i]; cp->im[i] = h[2 * i + 1]; }
+        for (int i = 0; i < n; ++i) fro += cp->re[i] * cp->re[i] + cp->im[i] * cp->im[i];
+    } else if (w->prec == QW_F32_COMP) {
+        auto *cp = reinterpret_cast<CoinP<ff> *>(w->coinp);
+        for (int i = 0; i < n; ++i) {
+            const float rh = (float)h[2 * i], ih = (float)h[2 * i + 1];
+            cp->re[i] = {rh, (float)(h[2 * i] - (double)rh)};
+            cp->im[i] = {ih, (float)(h[2 * i + 1] - (double)ih)};
+        }
+        fro = (double)d;    // hi + lo carries ~48 bits: no drift to compensate
+    } else {
+        auto *cp = reinterpret_cast<CoinP<float> *>(w->coinp);
+        for (int i = 0; i < n; ++i) { cp->re[i] = (float)h[2 * i]; cp->im[i] = (float)h[2 * i + 1]; }
+        for (int i = 0; i < n; ++i) fro += (double)cp->re[i] * cp->re[i] + (double)cp->im[i] * cp->im[i];
+    }
+    // For a unitary coin rounded to C_f, C_f^dagger C_f = alpha^2 I (exactly for
+    // rotation / Hadamard-type coins, to first order otherwise): every step scales
+    // the norm by alpha.  The kernels divide it back out.  A coin that is not
+    // close to unitary (|alpha - 1| > 1e-5, e.g. a deliberately lossy one) is
+    // applied as given.
+    const double alpha = std::sqrt(fro / d);
+    w->coin_alpha = std::fabs(alpha - 1.0) <= 1e-5 ? alpha : 1.0;
+    w->gain_fb = 1.0;
+
+    // Hadamard class on the cycle with the moving shift: C = lambda * M, M in
+    // {+-1}^{2x2}, M = diag(a, c) H diag(1, s) (needs m11 = -m10 m01 m00).
+    if (d == 2 && real && w->shift == QW_SHIFT_MOVING) {
+        double mag[4], lam = 0.0;
+        for (int i = 0; i < 4; ++i) { mag[i] = std::fabs(h[2 * i]); lam += mag[i] / 4; }
+        bool eq = lam > 0.0;
+        for (int i = 0; i < 4; ++i) eq = eq && std::fabs(mag[i] - lam) <= 1e-14 * lam;
+        if (eq) {
+            const int m00 = h[0] > 0 ? 1 : -1, m01 = h[2] > 0 ? 1 : -1;
+            const int m10 = h[4] > 0 ? 1 : -1, m11 = h[6] > 0 ? 1 : -1;
+            if (m11 == -m10 * m01 * m00) {
+                w->sign_lambda = lam;
+                w->sign_a = m00;
+                w->sign_s = m01 * m00;
+                w->sign_c = m10;
+                w->sign_sigma = w->sign_a * w->sign_s * w->sign_c;
+                w->kind = w->sign_sigma > 0 ? CK_SIGN_P : CK_SIGN_M;
+            }
+        }
+    }
+}
+
+static bool rounds_to_float(const qw_walk *w) {
+    return w->prec == QW_F32 || w->prec == QW_F32_BF16STORE;
+}
+
+// The factor that actually reaches the kernel for an ideal positive factor
+// `ideal`, with error feedback: the rounding residue of earlier launches is
+// folded into this one, so the product of applied factors tracks the product
+// of ideal ones to one rounding instead of one rounding per launch.
+static double feedback_gain(qw_walk *w, double ideal, bool update = true) {
+    if (ideal == 1.0 && w->gain_fb == 1.0) return 1.0;
+    const double want = ideal / w->gain_fb;
+    const double applied = rounds_to_float(w) ? (double)(float)want : want;
+    if (update) w->gain_fb *= applied / ideal;
+    return applied;
+}
+
+// Per-step norm-drift factor for the 2D and generic kernels.
+static double drift_gain(qw_walk *w, int steps, bool update = true) {
+    if (w->kind == CK_PERSITE || w->kind == CK_PHASE || w->coin_alpha == 1.0) return 1.0;
+    return feedback_gain(w, std::pow(w->coin_alpha, -(double)steps), update);
+}
+
+// Pre / post per-plane factors of one 1D launch of K steps.
+static void launch_gains_1d(qw_walk *w, int K, int adj, Step1DArgs &a, bool update = true) {
+    if (w->kind == CK_SIGN_P || w->kind == CK_SIGN_M) {
+        const double mag = feedback_gain(w, std::pow(w->sign_lambda, (double)K), update);
+        const double ak1 = ((K - 1) % 2 == 0 || w->sign_a > 0) ? 1.0 : -1.0;   // a^{K-1}
+        if (!adj) {
+            a.pre0 = 1.0; a.pre1 = (double)(w->sign_sigma * w->sign_s);
+            a.post0 = mag * ak1 * w->sign_a; a.post1 = mag * ak1 * w->sign_c;
+        } else {
+            a.pre0 = (double)w->sign_a; a.pre1 = (double)(w->sign_sigma * w->sign_c);
+            a.post0 = mag * ak1; a.post1 = mag * ak1 * w->sign_s;
+        }
+        return;
+    }
+    const double g = drift_gain(w, K, update);
+    a.pre0 = a.pre1 = 1.0;
+    a.post0 = a.post1 = g;
+}
+
+static qw_status ensure_staging(qw_walk *w, size_t bytes) {
+    if (w->staging_bytes >= bytes) return QW_OK;
+    if (w->staging) { cudaStreamSynchronize(w->stream); cudaFree(w->staging); w->staging = nullptr; w->staging_bytes = 0; }
+    cudaError_t e = dev_alloc(&w->staging, bytes);
+    if (e != cudaSuccess) return cuda_error(w, e, "staging allocation");
+    w->staging_bytes = bytes;
+    return QW_OK;
+}
+
+static constexpr size_t STAGE_CHUNK = size_t(32) << 20;  // bytes per host conversion chunk
+
+qw_status run_steps(qw_walk *w, int64_t T, int adj) {
+    if (T < 0) return set_error(w, QW_EINVAL, "T must be >= 0");
+    if (T == 0) return QW_OK;
+    const void *cp = w->coinp;
+    bool generic = w->bc != QW_BC_PERIODIC || w->has_links;
+    if (!generic && w->ndim == 2) {
+        if (w->kind == CK_PERSITE) generic = true;
+        if (w->kind == CK_PHASE && !(w->prec == QW_F32 || w->prec == QW_F64)) generic = true;
+    }
+    cudaError_t e = cudaSuccess;
+    if (generic) {
+        StepGenericArgs a{};
+        a.ndim = w->ndim; a.nx = w->nx; a.ny = w->ny; a.shift = w->shift; a.bc = w->bc;
+        a.kind = w->kind; a.coins = w->coins_dev; a.phi = w->phi_dev;
+        a.links = w->has_links ? w->links_dev : nullptr; a.adjoint = adj;
+        if (w->kind == CK_SIGN_P || w->kind == CK_SIGN_M) a.kind = CK_COMPLEX;   // generic reads the matrix
+        for (int64_t t = 0; t < T; ++t) {
+            a.gain = drift_gain(w, 1);
+            a.in = cur_view(w); a.out = next_view(w);
+            if ((e = stepgen(w->prec, a, cp, w->stream)) != cudaSuccess) return cuda_error(w, e, "generic step launch");
+            w->cur ^= 1;
+        }
+        return QW_OK;
+    }
+    if (w->ndim == 1) {
+        int K, tile;
+        effective_plan(w, K, tile);
+        const int teff = tile1d(w->prec, tile, w->kind, adj);
+        K = std::min(K, 8 * teff);
+        Step1DArgs a{};
+        a.n = w->nx; a.tile = teff; a.shift = w->shift; a.kind = w->kind; a.coins = w->coins_dev;
+        for (int64_t rem = T; rem > 0;) {
+            a.K = (int)std::min<int64_t>(K, rem);
+            launch_gains_1d(w, a.K, adj, a);
+            a.in = cur_view(w); a.out = next_view(w);
+            if ((e = step1d(w->prec, a, cp, adj, w->stream)) != cudaSuccess) return cuda_error(w, e, "1D step launch");
+            w->cur ^= 1;
+            rem -= a.K;
+        }
+        return QW_OK;
+    }
+    Step2DArgs a{};
+    a.nx = w->nx; a.ny = w->ny; a.shift = w->shift; a.kind = w->kind; a.coins = w->coins_dev;
+    a.phi = w->phi_dev; a.K = 1;
+    for (int64_t t = 0; t < T; ++t) {
+        a.gain = drift_gain(w, 1);
+        a.in = cur_view(w); a.out = next_view(w);
+        if ((e = step2d(w->prec, a, cp, adj, w->stream)) != cudaSuccess) return cuda_error(w, e, "2D step launch");
+        w->cur ^= 1;
+    }
+    return QW_OK;
+}
+
+}  // namespace qw
+
+// ------------------------------------------------------------------ ABI
+extern "C" {
+
+const char *qw_version(void) { return "qw 0.1 sm_103a"; }
+
+const char *qw_status_string(qw_status s) {
+    switch (s) {
+        case QW_OK: return "ok";
+        case QW_EINVAL: return "invalid argument";
+        case QW_ENOMEM: return "out of memory";
+        case QW_ECUDA: return "CUDA error";
+        case QW_ESTATE: return "invalid state for this call";
+        case QW_ETIMEOUT: return "device wait timed out";
+        case QW_EUNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *qw_last_error(const qw_walk *w) { return w ? w->err.c_str() : "null handle"; }
+
+qw_status qw_destroy(qw_walk *w) {
+    if (!w) return QW_OK;
+    cudaStreamSynchronize(w->stream);
+    cudaFree(w->buf[0]);
+    cudaFree(w->buf[1]);
+    cudaFree(w->coins_dev);
+    cudaFree(w->phi_dev);
+    cudaFree(w->links_dev);
+    cudaFree(w->partials);
+    cudaFree(w->norm_dev);
+    cudaFree(w->p_dev);
+    cudaFree(w->staging);
+    cudaFree(w->grad_scratch);
+    if (w->host_scalar) cudaFreeHost(w->host_scalar);
+    delete w;
+    return QW_OK;
+}
+
+qw_status qw_create(int ndim, const int64_t *dims, int coin_dim, qw_boundary bc, qw_shift shift,
+                    qw_precision prec, void *cuda_stream, qw_walk **out) {
+    if (!out) return QW_EINVAL;
+    *out = nullptr;
+    if ((ndim != 1 && ndim != 2) || !dims || coin_dim != 2 * ndim) return QW_EINVAL;
+    if (dims[0] < 1 || (ndim == 2 && dims[1] < 1)) return QW_EINVAL;
+    if ((int)bc < 0 || (int)bc > 2 || (int)shift < 0 || (int)shift > 1 || (int)prec < 0 || (int)prec > 3)
+        return QW_EINVAL;
+    const int64_t nx = dims[0], ny = ndim == 2 ? dims[1] : 1;
+    if (nx > (int64_t(1) << 40) || ny > (int64_t(1) << 40) || nx * ny > (int64_t(1) << 40)) return QW_EINVAL;
+
+    qw_walk *w = new (std::nothrow) qw_walk();
+    if (!w) return QW_ENOMEM;
+    w->ndim = ndim; w->d = coin_dim; w->nx = nx; w->ny = ny; w->ns = nx * ny;
+    w->bc = bc; w->shift = shift; w->prec = prec;
+    w->stream = static_cast<cudaStream_t>(cuda_stream);
+    w->pitch = (w->ns + 63) / 64 * 64;
+    w->nslots = w->d * (prec == QW_F32_COMP ? 2 : 1);
+    w->slot_bytes = slot_bytes_of(prec);
+    w->state_bytes = (size_t)w->nslots * w->pitch * w->slot_bytes;
+
+    cudaError_t e = cudaGetDevice(&w->device);
+    if (e == cudaSuccess) e = dev_alloc(&w->buf[0], w->state_bytes);
+    if (e == cudaSuccess) e = dev_alloc(&w->buf[1], w->state_bytes);
+    if (e == cudaSuccess) e = dev_alloc((void **)&w->partials, sizeof(double) * marginal_blocks());
+    if (e == cudaSuccess) e = dev_alloc((void **)&w->norm_dev, sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&w->host_scalar, sizeof(double) * 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w->buf[0], 0, w->state_bytes, w->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w->buf[1], 0, w->state_bytes, w->stream);
+    if (e != cudaSuccess) {
+        qw_status st = e == cudaErrorMemoryAllocation ? QW_ENOMEM : QW_ECUDA;
+        (void)cudaGetLastError();
+        qw_destroy(w);
+        return st;
+    }
+    double ident[32] = {0};
+    for (int i = 0; i < coin_dim; ++i) ident[2 * (i * coin_dim + i)] = 1.0;
+    apply_global_coin(w, ident);
+    *out = w;
+    return QW_OK;
+}
+
+int64_t qw_nsites(const qw_walk *w) { return w ? w->ns : -1; }
+
+qw_status qw_synchronize(qw_walk *w) {
+    if (!w) return QW_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(w->stream);
+    return e == cudaSuccess ? QW_OK : cuda_error(w, e, "synchronize");
+}
+
+qw_status qw_set_coin(qw_walk *w, const double *coin, int per_site, int on_device) {
+    if (!w) return QW_EINVAL;
+    if (!coin) return set_error(w, QW_EINVAL, "coin is NULL");
+    const int d = w->d;
+    cudaError_t e;
+    if (!per_site) {
+        double h[32];
+        if (on_device) {
+            e = cudaMemcpyAsync(h, coin, sizeof(double) * 2 * d * d, cudaMemcpyDeviceToHost, w->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
+            if (e != cudaSuccess) return cuda_error(w, e, "coin copy");
+        } else {
+            std::memcpy(h, coin, sizeof(double) * 2 * d * d);
+        }
+        apply_global_coin(w, h);
+        return QW_OK;
+    }
+    const int64_t count = w->ns * d * d;   // complex entries
+    const size_t want = (size_t)count * 2 * real_bytes(w->prec);
+    if (w->coins_bytes != want) {
+        cudaStreamSynchronize(w->stream);
+        cudaFree(w->coins_dev);
+        w->coins_dev = nullptr; w->coins_bytes = 0;
+        if ((e = dev_alloc(&w->coins_dev, want)) != cudaSuccess) return cuda_error(w, e, "per-site coin allocation");
+        w->coins_bytes = want;
+    }
+    if (on_device) {
+        if ((e = launch_convert_coins(w->prec, coin, w->coins_dev, count, w->stream)) != cudaSuccess)
+            return cuda_error(w, e, "coin conversion");
+    } else {
+        qw_status st = ensure_staging(w, STAGE_CHUNK);
+        if (st != QW_OK) return st;
+        const int64_t per = (int64_t)(STAGE_CHUNK / 16);
+        for (int64_t off = 0; off < count; off += per) {
+            const int64_t n = std::min(per, count - off);
+            e = cudaMemcpyAsync(w->staging, coin + 2 * off, (size_t)n * 16, cudaMemcpyHostToDevice, w->stream);
+            if (e == cudaSuccess)
+                e = launch_convert_coins(w->prec, (const double *)w->staging,
+                                         (char *)w->coins_dev + (size_t)off * 2 * real_bytes(w->prec), n, w->stream);
+            if (e != cudaSuccess) return cuda_error(w, e, "coin upload");
+        }
+    }
+    w->kind = CK_PERSITE;
+    return QW_OK;
+}
+
+qw_status qw_set_coin_phases(qw_walk *w, const double *base, const float *phi, int on_device) {
+    if (!w) return QW_EINVAL;
+    if (!base || !phi) return set_error(w, QW_EINVAL, "base and phi are required");
+    const int d = w->d;
+    const size_t pbytes = sizeof(float) * (size_t)w->ns * d;
+    cudaError_t e;
+    if (!w->phi_dev) {
+        if ((e = dev_alloc((void **)&w->phi_dev, pbytes)) != cudaSuccess) return cuda_error(w, e, "phase allocation");
+    }
+    e = cudaMemcpyAsync(w->phi_dev, phi, pbytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, w->stream);
+    if (e != cudaSuccess) return cuda_error(w, e, "phase copy");
+    apply_global_coin(w, base);   // the kernels read the base coin from here
+    if (w->ndim == 2) {
+        w->kind = CK_PHASE;
+        return QW_OK;
+    }
+    // 1D: expand to per-site matrices once
+    const size_t want = (size_t)w->ns * d * d * 2 * real_bytes(w->prec);
+    if (w->coins_bytes != want) {
+        cudaStreamSynchronize(w->stream);
+        cudaFree(w->coins_dev);
+        w->coins_dev = nullptr; w->coins_bytes = 0;
+        if ((e = dev_alloc(&w->coins_dev, want)) != cudaSuccess) return cuda_error(w, e, "per-site coin allocation");
+        w->coins_bytes = want;
+    }
+    qw_status st = ensure_staging(w, 256);
+    if (st != QW_OK) return st;
+    e = cudaMemcpyAsync(w->staging, base, sizeof(double) * 2 * d * d, cudaMemcpyHostToDevice, w->stream);
+    if (e == cudaSuccess) e = launch_phase_coins(w->prec, (const double *)w->staging, w->phi_dev, w->coins_dev, w->ns, d, w->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);  // base lives on the caller's stack
+    if (e != cudaSuccess) return cuda_error(w, e, "phase coin expansion");
+    w->kind = CK_PERSITE;
+    return QW_OK;
+}
+
+qw_status qw_set_links(qw_walk *w, const uint8_t *closed, int on_device) {
+    if (!w) return QW_EINVAL;
+    if (!closed) { w->has_links = false; return QW_OK; }
+    const size_t bytes = (size_t)w->ndim * w->ns;
+    cudaError_t e;
+    if (!w->links_dev && (e = dev_alloc((void **)&w->links_dev, bytes)) != cudaSuccess)
+        return cuda_error(w, e, "link mask allocation");
+    e = cudaMemcpyAsync(w->links_dev, closed, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, w->stream);
+    if (e != cudaSuccess) return cuda_error(w, e, "link mask copy");
+    if (!on_device && (e = cudaStreamSynchronize(w->stream)) != cudaSuccess) return cuda_error(w, e, "link mask copy");
+    w->has_links = true;
+    return QW_OK;
+}
+
+static bool direct_layout(const qw_walk *w, qw_cdtype dt) {
+    return (w->prec == QW_F32 && dt == QW_C64) || (w->prec == QW_F64 && dt == QW_C128);
+}
+
+qw_status qw_set_state(qw_walk *w, const void *amp, qw_cdtype dtype, int on_device) {
+    if (!w) return QW_EINVAL;
+    if (!amp || (dtype != QW_C128 && dtype != QW_C64)) return set_error(w, QW_EINVAL, "bad state buffer or dtype");
+    const size_t eb = dtype == QW_C128 ? 16 : 8;
+    const size_t plane = (size_t)w->ns * eb;
+    cudaError_t e = cudaSuccess;
+    const View dst = cur_view(w);
+    w->gain_fb = 1.0;
+    if (direct_layout(w, dtype)) {
+        e = cudaMemcpy2DAsync(w->buf[w->cur], (size_t)w->pitch * w->slot_bytes, amp, plane, plane, w->d,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, w->stream);
+        if (e != cudaSuccess) return cuda_error(w, e, "state copy");
+        return QW_OK;
+    }
+    if (w->prec == QW_F32_COMP) {  // clear the lo slots first (a complex64 input has none)
+        e = cudaMemsetAsync((char *)w->buf[w->cur] + (size_t)w->d * w->pitch * w->slot_bytes, 0,
+                            (size_t)w->d * w->pitch * w->slot_bytes, w->stream);
+        if (e != cudaSuccess) return cuda_error(w, e, "state clear");
+    }
+    for (int c = 0; c < w->d; ++c) {
+        const char *src = static_cast<const char *>(amp) + c * plane;
+        if (on_device) {
+            if ((e = launch_import(w->prec, dst, w->ns, src, dtype == QW_C64, 0, w->ns, c, w->stream)) != cudaSuccess)
+                return cuda_error(w, e, "state import");
+            continue;
+        }
+        qw_status st = ensure_staging(w, STAGE_CHUNK);
+        if (st != QW_OK) return st;
+        const int64_t per = (int64_t)(STAGE_CHUNK / eb);
+        for (int64_t off = 0; off < w->ns; off += per) {
+            const int64_t n = std::min(per, w->ns - off);
+            e = cudaMemcpyAsync(w->staging, src + off * eb, (size_t)n * eb, cudaMemcpyHostToDevice, w->stream);
+            if (e == cudaSuccess) e = launch_import(w->prec, dst, w->ns, w->staging, dtype == QW_C64, off, n, c, w->stream);
+            if (e != cudaSuccess) return cuda_error(w, e, "state upload");
+        }
+    }
+    return QW_OK;
+}
+
+qw_status qw_get_state(qw_walk *w, void *amp_out, qw_cdtype dtype, int on_device) {
+    if (!w) return QW_EINVAL;
+    if (!amp_out || (dtype != QW_C128 && dtype != QW_C64)) return set_error(w, QW_EINVAL, "bad state buffer or dtype");
+    const size_t eb = dtype == QW_C128 ? 16 : 8;
+    const size_t plane = (size_t)w->ns * eb;
+    cudaError_t e = cudaSuccess;
+    const View src = cur_view(w);
+    if (direct_layout(w, dtype)) {
+        e = cudaMemcpy2DAsync(amp_out, plane, w->buf[w->cur], (size_t)w->pitch * w->slot_bytes, plane, w->d,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, w->stream);
+        if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(w->stream);
+        return e == cudaSuccess ? QW_OK : cuda_error(w, e, "state copy");
+    }
+    for (int c = 0; c < w->d; ++c) {
+        char *dst = static_cast<char *>(amp_out) + c * plane;
+        if (on_device) {
+            if ((e = launch_export(w->prec, src, w->ns, dst, dtype == QW_C64, 0, w->ns, c, w->stream)) != cudaSuccess)
+                return cuda_error(w, e, "state export");
+            continue;
+        }
+        qw_status st = ensure_staging(w, STAGE_CHUNK);
+        if (st != QW_OK) return st;
+        const int64_t per = (int64_t)(STAGE_CHUNK / eb);
+        for (int64_t off = 0; off < w->ns; off += per) {
+            const int64_t n = std::min(per, w->ns - off);
+            e = launch_export(w->prec, src, w->ns, w->staging, dtype == QW_C64, off, n, c, w->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dst + off * eb, w->staging, (size_t)n * eb, cudaMemcpyDeviceToHost, w->stream);
+            if (e != cudaSuccess) return cuda_error(w, e, "state download");
+        }
+    }
+    if (!on_device && (e = cudaStreamSynchronize(w->stream)) != cudaSuccess) return cuda_error(w, e, "state download");
+    return QW_OK;
+}
+
+qw_status qw_step(qw_walk *w, int64_t T) {
+    if (!w) return QW_EINVAL;
+    return run_steps(w, T, 0);
+}
+
+qw_status qw_step_adjoint(qw_walk *w, int64_t T) {
+    if (!w) return QW_EINVAL;
+    return run_steps(w, T, 1);
+}
+
+qw_status qw_probabilities(qw_walk *w, void *P_out, qw_rdtype pdtype, int on_device, double *norm_out) {
+    if (!w) return QW_EINVAL;
+    if (pdtype != QW_R64 && pdtype != QW_R32) return set_error(w, QW_EINVAL, "bad probability dtype");
+    const size_t pb = (size_t)w->ns * (pdtype == QW_R32 ? 4 : 8);
+    void *pdst = nullptr;
+    cudaError_t e;
+    if (P_out) {
+        if (on_device) {
+            pdst = P_out;
+        } else {
+            if (w->p_bytes < pb) {
+                cudaStreamSynchronize(w->stream);
+                cudaFree(w->p_dev);
+                w->p_dev = nullptr; w->p_bytes = 0;
+                if ((e = dev_alloc(&w->p_dev, pb)) != cudaSuccess) return cuda_error(w, e, "probability buffer");
+                w->p_bytes = pb;
+            }
+            pdst = w->p_dev;
+        }
+    }
+    e = launch_marginals(w->prec, cur_view(w), w->ns, pdst, pdtype == QW_R32, w->partials, marginal_blocks(),
+                         w->norm_dev, w->stream);
+    if (e != cudaSuccess) return cuda_error(w, e, "marginal launch");
+    if (P_out && !on_device) {
+        if ((e = cudaMemcpyAsync(P_out, w->p_dev, pb, cudaMemcpyDeviceToHost, w->stream)) != cudaSuccess)
+            return cuda_error(w, e, "probability download");
+    }
+    if (norm_out) {
+        if ((e = cudaMemcpyAsync(w->host_scalar, w->norm_dev, sizeof(double), cudaMemcpyDeviceToHost, w->stream)) != cudaSuccess)
+            return cuda_error(w, e, "norm download");
+    }
+    if (norm_out || (P_out && !on_device)) {
+        if ((e = cudaStreamSynchronize(w->stream)) != cudaSuccess) return cuda_error(w, e, "marginals");
+        if (norm_out) *norm_out = *w->host_scalar;
+    }
+    return QW_OK;
+}
+
+qw_status qw_set_plan(qw_walk *w, int depth_k, int tile) {
+    if (!w) return QW_EINVAL;
+    if (depth_k == 0) { w->plan_k = 0; w->plan_tile = 0; w->plan_user = false; return QW_OK; }
+    if (depth_k < 0 || tile < 0) return set_error(w, QW_EINVAL, "negative plan");
+    if (w->ndim == 2) {
+        if (depth_k != 1) return set_error(w, QW_EUNSUPPORTED, "2D plans take k = 1");
+        w->plan_k = 1; w->plan_tile = 0; w->plan_user = true;
+        return QW_OK;
+    }
+    int dk, dt;
+    default_plan(w, dk, dt);
+    const int teff = tile1d(w->prec, tile ? tile : dt, CK_REAL, 0);
+    if (tile && teff != tile) return set_error(w, QW_EINVAL, "tile not compiled for this precision");
+    if (depth_k > 8 * teff) return set_error(w, QW_EINVAL, "k exceeds 8 * tile");
+    w->plan_k = depth_k; w->plan_tile = teff; w->plan_user = true;
+    return QW_OK;
+}
+
+qw_status qw_describe(const qw_walk *w, char *buf, size_t len) {
+    if (!w || !buf || !len) return QW_EINVAL;
+    static const char *kinds[] = {"real", "complex", "grover", "hadamard2", "per_site", "phase",
+                                  "hadamard_class", "hadamard_class"};
+    int k, t;
+    effective_plan(w, k, t);
+    if (w->ndim == 1) t = tile1d(w->prec, t, w->kind, 0);
+    const bool generic = w->bc != QW_BC_PERIODIC || w->has_links ||
+                         (w->ndim == 2 && (w->kind == CK_PERSITE ||
+                                           (w->kind == CK_PHASE && !(w->prec == QW_F32 || w->prec == QW_F64))));
+    std::snprintf(buf, len,
+                  "{\"ndim\": %d, \"sites\": %lld, \"coin_dim\": %d, \"precision\": %d, \"coin_kind\": \"%s\", "
+                  "\"k\": %d, \"tile\": %d, \"path\": \"%s\", \"state_bytes\": %zu}",
+                  w->ndim, (long long)w->ns, w->d, w->prec, kinds[w->kind], k, t,
+                  generic ? "generic" : (w->ndim == 1 ? "k_step1d" : "k_step2d"), w->state_bytes);
+    return QW_OK;
+}
+
+qw_status qw_get_plan(const qw_walk *w, int *depth_k, int *tile) {
+    if (!w || !depth_k || !tile) return QW_EINVAL;
+    int k, t;
+    effective_plan(w, k, t);
+    if (w->ndim == 1) t = tile1d(w->prec, t, w->kind, 0);
+    *depth_k = k;
+    *tile = t;
+    return QW_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ autotuner
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tune;  // key -> (tile, k)
+bool g_tune_loaded = false;
+
+std::string tune_key(const qw_walk *w) {
+    char b[128];
+    int lg = 0;
+    while ((int64_t(1) << (lg + 1)) <= w->ns) ++lg;
+    std::snprintf(b, sizeof b, "%dd_p%d_k%d_s%d_n2^%d", w->ndim, w->prec, w->kind, w->shift, lg);
+    return b;
+}
+
+void tune_load() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = std::getenv("QW_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char key[128];
+    int tile, k;
+    // format: one entry per line:  "key": [tile, k],
+    char line[256];
+    while (std::fgets(line, sizeof line, f)) {
+        if (std::sscanf(line, " \"%127[^\"]\": [%d, %d]", key, &tile, &k) == 3) g_tune[key] = {tile, k};
+    }
+    std::fclose(f);
+}
+
+void tune_save() {
+    const char *path = std::getenv("QW_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "w");
+    if (!f) return;
+    std::fprintf(f, "{\n");
+    size_t i = 0;
+    for (auto &kv : g_tune)
+        std::fprintf(f, "  \"%s\": [%d, %d]%s\n", kv.first.c_str(), kv.second.first, kv.second.second,
+                     ++i < g_tune.size() ? "," : "");
+    std::fprintf(f, "}\n");
+    std::fclose(f);
+}
+
+}  // namespace
+
+extern "C" qw_status qw_autotune(qw_walk *w, char *report, size_t report_len) {
+    if (!w) return QW_EINVAL;
+    auto put = [&](const char *s) {
+        if (report && report_len) { std::strncpy(report, s, report_len - 1); report[report_len - 1] = 0; }
+    };
+    if (w->ndim != 1 || w->bc != QW_BC_PERIODIC || w->has_links) {
+        put("{\"tuned\": false, \"reason\": \"only the periodic 1D kernel has a plan space\"}");
+        return QW_OK;
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_load();
+    const std::string key = tune_key(w);
+    auto it = g_tune.find(key);
+    char buf[512];
+    if (it != g_tune.end()) {
+        w->plan_tile = it->second.first;
+        w->plan_k = it->second.second;
+        std::snprintf(buf, sizeof buf, "{\"tuned\": true, \"cached\": true, \"key\": \"%s\", \"tile\": %d, \"k\": %d}",
+                      key.c_str(), w->plan_tile, w->plan_k);
+        put(buf);
+        return QW_OK;
+    }
+    int ta, tb;
+    tiles_of(w->prec, ta, tb);
+    const int tiles[2] = {ta, tb};
+    const int ks[] = {1, 2, 4, 8, 12, 16, 20, 24, 28, 32, 40, 48, 64, 96, 128};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_t = ta, best_k = 1;
+    Step1DArgs a{};
+    a.n = w->nx; a.shift = w->shift; a.kind = w->kind; a.coins = w->coins_dev;
+    a.in = cur_view(w); a.out = next_view(w);   // reads the state, writes only the scratch buffer
+    cudaError_t err = cudaSuccess;
+    for (int ti = 0; ti < 2; ++ti) {
+        const int teff = tile1d(w->prec, tiles[ti], w->kind, 0);
+        if (ti == 1 && teff == tile1d(w->prec, tiles[0], w->kind, 0)) break;  // kind has one tile only
+        for (int k : ks) {
+            if (k > 8 * teff) break;
+            a.tile = teff; a.K = k;
+            launch_gains_1d(w, k, 0, a, false);
+            err = step1d(w->prec, a, w->coinp, 0, w->stream);   // warm-up
+            if (err != cudaSuccess) break;
+            cudaEventRecord(e0, w->stream);
+            const int reps = 3;
+            for (int r = 0; r < reps; ++r) step1d(w->prec, a, w->coinp, 0, w->stream);
+            cudaEventRecord(e1, w->stream);
+            if ((err = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const float per_step = ms / (reps * k);
+            if (per_step < best) { best = per_step; best_t = teff; best_k = k; }
+        }
+        if (err != cudaSuccess) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_error(w, err, "autotune");
+    w->plan_tile = best_t;
+    w->plan_k = best_k;
+    g_tune[key] = {best_t, best_k};
+    tune_save();
+    std::snprintf(buf, sizeof buf,
+                  "{\"tuned\": true, \"cached\": false, \"key\": \"%s\", \"tile\": %d, \"k\": %d, \"ms_per_step\": %.6g}",
+                  key.c_str(), best_t, best_k, best);
+    put(buf);
+    return QW_OK;
+}
+
+// ------------------------------------------------------------------ bounded wait self test
+__global__ void k_bounded_wait(volatile int *flag, long long spins, int *status) {
+    long long i = 0;
+    while (i < spins && *flag == 0) {
+        __nanosleep(100);
+        ++i;
+    }
+    *status = (*flag == 0) ? 1 : 0;
+}
+
+extern "C" qw_status qw_debug_bounded_wait(int64_t spins, void *cuda_stream) {
+    if (spins < 0) return QW_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int *mem = nullptr;
+    cudaError_t e = dev_alloc((void **)&mem, 2 * sizeof(int));
+    if (e != cudaSuccess) { (void)cudaGetLastError(); return e == cudaErrorMemoryAllocation ? QW_ENOMEM : QW_ECUDA; }
+    int host[2] = {0, 0};
+    e = cudaMemsetAsync(mem, 0, 2 * sizeof(int), s);
+    if (e == cudaSuccess) {
+        k_bounded_wait<<<1, 1, 0, s>>>(mem, (long long)spins, mem + 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, mem, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(mem);
+    if (e != cudaSuccess) { (void)cudaGetLastError(); return QW_ECUDA; }
+    return host[1] ? QW_ETIMEOUT : QW_OK;
+}

@@ -1,0 +1,325 @@
+"""Python binding of the C ABI in ``include/qw.h`` (argument marshalling only).
+
+Every function named ``qw_*`` here calls the library function of the same name
+through ctypes; the classes ``Walk`` and ``Batch`` and the autograd Function
+``RegionMass`` only hold handles and pass ``tensor.data_ptr()`` and the current
+torch CUDA stream.  All arithmetic of the walk runs in the library's kernels;
+there is no CPU fallback: if ``libqw.so`` is missing, loading raises.
+
+The walk (Sawerwain & Gielerak, arXiv:1003.3779, Sec. 2.1): one step is
+U = S (I (x) C) on the cycle (coin dim 2) or torus (coin dim 4).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libqw.so")
+
+QW_OK, QW_EINVAL, QW_ENOMEM, QW_ECUDA, QW_ESTATE, QW_ETIMEOUT, QW_EUNSUPPORTED = range(7)
+BC_PERIODIC, BC_SEGMENT, BC_LINE = 0, 1, 2
+SHIFT_MOVING, SHIFT_FLIPFLOP = 0, 1
+F64, F32, F32_BF16STORE, F32_COMP = 0, 1, 2, 3
+C128, C64 = 0, 1
+R64, R32 = 0, 1
+
+PRECISIONS = {"f64": F64, "f32": F32, "bf16": F32_BF16STORE, "comp": F32_COMP}
+
+_lib = None
+
+
+class QWError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(msg)
+        self.status = status
+
+
+def lib():
+    """Load libqw.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libqw.so not found at {LIB_PATH}: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, I64, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    sig = {
+        "qw_create": (I, [I, P, I, I, I, I, P, P]),
+        "qw_destroy": (I, [P]),
+        "qw_set_coin": (I, [P, P, I, I]),
+        "qw_set_coin_phases": (I, [P, P, P, I]),
+        "qw_set_links": (I, [P, P, I]),
+        "qw_set_state": (I, [P, P, I, I]),
+        "qw_get_state": (I, [P, P, I, I]),
+        "qw_step": (I, [P, I64]),
+        "qw_step_adjoint": (I, [P, I64]),
+        "qw_probabilities": (I, [P, P, I, I, P]),
+        "qw_set_plan": (I, [P, I, I]),
+        "qw_get_plan": (I, [P, P, P]),
+        "qw_autotune": (I, [P, ctypes.c_char_p, S]),
+        "qw_nsites": (I64, [P]),
+        "qw_describe": (I, [P, ctypes.c_char_p, S]),
+        "qw_synchronize": (I, [P]),
+        "qw_backward": (I, [P, P, I64, I64, P, P, I]),
+        "qw_batch_create": (I, [I, P, P, P, P, P, I, P, P]),
+        "qw_batch_step": (I, [P]),
+        "qw_batch_probabilities": (I, [P, P, I, P]),
+        "qw_batch_get_state": (I, [P, I, P, I]),
+        "qw_batch_destroy": (I, [P]),
+        "qw_status_string": (ctypes.c_char_p, [I]),
+        "qw_last_error": (ctypes.c_char_p, [P]),
+        "qw_batch_last_error": (ctypes.c_char_p, [P]),
+        "qw_version": (ctypes.c_char_p, []),
+        "qw_debug_bounded_wait": (I, [I64, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def declared_symbols():
+    """Entry points the binding expects (matches include/qw.h)."""
+    lib()
+    return sorted(n for n in dir(_lib) if n.startswith("qw_"))
+
+
+def _check(st, handle=None, batch=False):
+    if st == QW_OK:
+        return
+    L = lib()
+    msg = L.qw_status_string(st).decode()
+    if handle is not None:
+        detail = (L.qw_batch_last_error(handle) if batch else L.qw_last_error(handle)).decode()
+        if detail:
+            msg = f"{msg}: {detail}"
+    raise QWError(st, msg)
+
+
+def _ptr(x):
+    """Pointer of a numpy array or torch tensor (or None)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _on_device(x):
+    return 0 if isinstance(x, np.ndarray) else int(x.is_cuda)
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# ---------------------------------------------------------------- raw ABI
+def qw_version():
+    return lib().qw_version().decode()
+
+
+def qw_create(ndim, dims, coin_dim, bc=BC_PERIODIC, shift=SHIFT_MOVING, prec=F32, stream=None):
+    d = np.ascontiguousarray(dims, dtype=np.int64)
+    h = ctypes.c_void_p()
+    st = lib().qw_create(int(ndim), _ptr(d), int(coin_dim), int(bc), int(shift), int(prec),
+                         stream if stream is not None else _stream(), ctypes.byref(h))
+    _check(st)
+    return h
+
+
+def qw_destroy(h):
+    _check(lib().qw_destroy(h))
+
+
+def qw_set_coin(h, coin, per_site=False):
+    if isinstance(coin, np.ndarray):
+        coin = np.ascontiguousarray(coin, dtype=np.complex128)
+    _check(lib().qw_set_coin(h, _ptr(coin), int(per_site), _on_device(coin)), h)
+
+
+def qw_set_coin_phases(h, base, phi):
+    base = np.ascontiguousarray(base, dtype=np.complex128)
+    if isinstance(phi, np.ndarray):
+        phi = np.ascontiguousarray(phi, dtype=np.float32)
+    _check(lib().qw_set_coin_phases(h, _ptr(base), _ptr(phi), _on_device(phi)), h)
+
+
+def qw_set_links(h, closed):
+    if isinstance(closed, np.ndarray):
+        closed = np.ascontiguousarray(closed, dtype=np.uint8)
+    _check(lib().qw_set_links(h, _ptr(closed), _on_device(closed) if closed is not None else 0), h)
+
+
+def _cdtype(x):
+    if isinstance(x, np.ndarray):
+        return C64 if x.dtype == np.complex64 else C128
+    import torch
+    return C64 if x.dtype == torch.complex64 else C128
+
+
+def qw_set_state(h, amp):
+    if isinstance(amp, np.ndarray) and amp.dtype not in (np.complex64, np.complex128):
+        amp = amp.astype(np.complex128)
+    if isinstance(amp, np.ndarray):
+        amp = np.ascontiguousarray(amp)
+    _check(lib().qw_set_state(h, _ptr(amp), _cdtype(amp), _on_device(amp)), h)
+
+
+def qw_get_state(h, out):
+    _check(lib().qw_get_state(h, _ptr(out), _cdtype(out), _on_device(out)), h)
+    return out
+
+
+def qw_step(h, T):
+    _check(lib().qw_step(h, int(T)), h)
+
+
+def qw_step_adjoint(h, T):
+    _check(lib().qw_step_adjoint(h, int(T)), h)
+
+
+def qw_probabilities(h, P_out=None, want_norm=True):
+    norm = ctypes.c_double(0.0)
+    pd = R64
+    if P_out is not None:
+        if isinstance(P_out, np.ndarray):
+            pd = R32 if P_out.dtype == np.float32 else R64
+        else:
+            import torch
+            pd = R32 if P_out.dtype == torch.float32 else R64
+    st = lib().qw_probabilities(h, _ptr(P_out), pd, _on_device(P_out) if P_out is not None else 0,
+                                ctypes.byref(norm) if want_norm else None)
+    _check(st, h)
+    return norm.value if want_norm else None
+
+
+def qw_set_plan(h, k, tile=0):
+    _check(lib().qw_set_plan(h, int(k), int(tile)), h)
+
+
+def qw_get_plan(h):
+    k, t = ctypes.c_int(), ctypes.c_int()
+    _check(lib().qw_get_plan(h, ctypes.byref(k), ctypes.byref(t)), h)
+    return k.value, t.value
+
+
+def qw_autotune(h):
+    buf = ctypes.create_string_buffer(512)
+    _check(lib().qw_autotune(h, buf, 512), h)
+    return buf.value.decode()
+
+
+def qw_describe(h):
+    import json
+    buf = ctypes.create_string_buffer(512)
+    _check(lib().qw_describe(h, buf, 512), h)
+    return json.loads(buf.value.decode())
+
+
+def qw_synchronize(h):
+    _check(lib().qw_synchronize(h), h)
+
+
+def qw_backward(h, rect, T, K, grad_out):
+    r = np.ascontiguousarray(rect, dtype=np.int64)
+    loss = ctypes.c_double(0.0)
+    _check(lib().qw_backward(h, _ptr(r), int(T), int(K), ctypes.byref(loss), _ptr(grad_out),
+                             _on_device(grad_out)), h)
+    return loss.value
+
+
+def qw_debug_bounded_wait(spins, stream=None):
+    return lib().qw_debug_bounded_wait(int(spins), stream if stream is not None else _stream())
+
+
+# ---------------------------------------------------------------- convenience
+class Walk:
+    """A walk handle: the lattice, its coin and its state live on the GPU.
+
+    ``Walk((N,))`` is the cycle Z_N (coin dim 2); ``Walk((Lx, Ly))`` the torus
+    (coin dim 4).  ``prec`` is one of "f64", "f32", "bf16", "comp".
+    """
+
+    def __init__(self, dims, prec="f32", shift=SHIFT_MOVING, bc=BC_PERIODIC, stream=None):
+        dims = tuple(int(x) for x in dims)
+        self.ndim = len(dims)
+        self.dims = dims
+        self.d = 2 * self.ndim
+        self.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        self.h = qw_create(self.ndim, dims, self.d, bc, shift, self.prec, stream)
+        self.nsites = int(np.prod(dims))
+
+    @property
+    def plane_shape(self):
+        return (self.nsites,) if self.ndim == 1 else (self.dims[1], self.dims[0])
+
+    def close(self):
+        if getattr(self, "h", None):
+            qw_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_coin(self, coin, per_site=False):
+        qw_set_coin(self.h, coin, per_site)
+        return self
+
+    def set_coin_phases(self, base, phi):
+        qw_set_coin_phases(self.h, base, phi)
+        return self
+
+    def set_links(self, closed):
+        qw_set_links(self.h, closed)
+        return self
+
+    def set_state(self, amp):
+        qw_set_state(self.h, amp)
+        return self
+
+    def state(self, dtype=np.complex128):
+        out = np.empty((self.d,) + self.plane_shape, dtype=dtype)
+        qw_get_state(self.h, out)
+        return out
+
+    def step(self, T):
+        qw_step(self.h, T)
+        return self
+
+    def step_adjoint(self, T):
+        qw_step_adjoint(self.h, T)
+        return self
+
+    def probabilities(self, dtype=np.float64):
+        P = np.empty(self.plane_shape, dtype=dtype)
+        norm = qw_probabilities(self.h, P)
+        return P, norm
+
+    def norm(self):
+        return qw_probabilities(self.h, None)
+
+    def set_plan(self, k, tile=0):
+        qw_set_plan(self.h, k, tile)
+        return self
+
+    def plan(self):
+        return qw_get_plan(self.h)
+
+    def autotune(self):
+        return qw_autotune(self.h)
+
+    def describe(self):
+        return qw_describe(self.h)
+
+    def synchronize(self):
+        qw_synchronize(self.h)

@@ -1,0 +1,153 @@
+"""GPU parity on the torus (coin dim 4) and for the general boundary / broken-link
+path: the CUDA path through the C ABI against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1003_3779_gb300 import inputs
+from tests.helpers import amp_tol, l1, maxabs, p_l1_tol
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["f64", "f32", "bf16", "comp"]
+
+
+@pytest.fixture(scope="module")
+def qw():
+    import paper_1003_3779_gb300.qw as qw
+    qw.lib()
+    return qw
+
+
+def coin_named(name, rng):
+    if name == "grover":
+        return inputs.grover()
+    if name == "hh":
+        return inputs.hadamard2()
+    if name == "fourier":
+        return inputs.fourier()
+    if name == "real":
+        q, _ = np.linalg.qr(rng.standard_normal((4, 4)))
+        return q.astype(np.complex128)
+    return inputs.random_unitary(4, rng)
+
+
+def gpu_run(qw, psi0, coin, T, prec, shift=0, adjoint=False, per_site=False, phases=None, bc=0,
+            links=None):
+    d, Ly, Lx = psi0.shape
+    w = qw.Walk((Lx, Ly), prec=prec, shift=shift, bc=bc)
+    if phases is not None:
+        w.set_coin_phases(coin, phases)
+    else:
+        w.set_coin(coin, per_site=per_site)
+    if links is not None:
+        w.set_links(links)
+    w.set_state(psi0)
+    (w.step_adjoint if adjoint else w.step)(T)
+    out = w.state()
+    P, norm = w.probabilities()
+    w.close()
+    return out, P, norm
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("coin", ["grover", "hh", "real", "complex", "fourier"])
+@pytest.mark.parametrize("shift", [0, 1])
+def test_torus_coins_shifts(qw, prec, coin, shift):
+    rng = np.random.default_rng(["grover", "hh", "real", "complex", "fourier"].index(coin) * 2 + shift)
+    C = coin_named(coin, rng)
+    Lx, Ly, T = 136, 18, 23          # 136 = one full 128-site segment + a ragged tail
+    psi0 = inputs.random_state((4, Ly, Lx), seed=21)
+    want = oracle.evolve(psi0, C, T, shift=shift)
+    got, P, _ = gpu_run(qw, psi0, C, T, prec, shift=shift)
+    assert maxabs(got, want) < amp_tol(prec, T)
+    assert l1(P, oracle.probabilities(want)[0]) < p_l1_tol(prec, T, Lx * Ly)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_grover_from_origin_symmetry(qw, prec):
+    L, T = 256, 100
+    psi0 = inputs.localized_2d(L)
+    want = oracle.evolve(psi0, inputs.grover(), T)
+    got, P, norm = gpu_run(qw, psi0, inputs.grover(), T, prec)
+    assert maxabs(got, want) < amp_tol(prec, T)
+    if prec != "bf16":
+        neg = (-np.arange(L)) % L
+        assert maxabs(P, P.T) < 1e-6 and maxabs(P, P[neg][:, neg]) < 1e-6
+        y, x = np.mgrid[0:L, 0:L]
+        assert np.all(P[(x + y - T) % 2 != 0] == 0)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("coin", ["grover", "hh", "complex", "real"])
+@pytest.mark.parametrize("shift", [0, 1])
+def test_torus_adjoint(qw, prec, coin, shift):
+    rng = np.random.default_rng(31)
+    C = coin_named(coin, rng)
+    Lx, Ly, T = 260, 7, 15
+    psi0 = inputs.random_state((4, Ly, Lx), seed=22)
+    want = oracle.evolve(psi0, C, T, shift=shift, adjoint=True)
+    got, _, _ = gpu_run(qw, psi0, C, T, prec, shift=shift, adjoint=True)
+    assert maxabs(got, want) < amp_tol(prec, T)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shift", [0, 1])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_phase_coin_2d(qw, prec, shift, adjoint):
+    Lx, Ly, T = 128, 40, 12
+    rng = np.random.default_rng(41)
+    phi = rng.uniform(-0.5, 0.5, size=(Ly, Lx, 4)).astype(np.float32)
+    psi0 = inputs.random_state((4, Ly, Lx), seed=23)
+    want = oracle.evolve(psi0, inputs.grover(), T, shift=shift, phi=phi.reshape(-1, 4).astype(np.float64),
+                         adjoint=adjoint)
+    got, _, _ = gpu_run(qw, psi0, inputs.grover(), T, prec, shift=shift, adjoint=adjoint,
+                        phases=phi.reshape(-1, 4))
+    assert maxabs(got, want) < amp_tol(prec, T) + (T * 2e-7 if prec in ("f32", "bf16") else 0)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_per_site_matrices_2d(qw, prec):
+    Lx, Ly, T = 9, 6, 7
+    rng = np.random.default_rng(51)
+    coins = np.stack([inputs.random_unitary(4, rng) for _ in range(Lx * Ly)])
+    psi0 = inputs.random_state((4, Ly, Lx), seed=24)
+    for shift in (0, 1):
+        for adj in (False, True):
+            want = oracle.evolve(psi0, coins, T, shift=shift, adjoint=adj)
+            got, _, _ = gpu_run(qw, psi0, coins, T, prec, shift=shift, per_site=True, adjoint=adj)
+            assert maxabs(got, want) < amp_tol(prec, T)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "comp"])
+@pytest.mark.parametrize("bc", [0, 1, 2])
+@pytest.mark.parametrize("shift", [0, 1])
+@pytest.mark.parametrize("ndim", [1, 2])
+def test_boundaries_and_broken_links(qw, prec, bc, shift, ndim):
+    rng = np.random.default_rng(61 + bc + 3 * shift + 7 * ndim)
+    shape = (2, 301) if ndim == 1 else (4, 13, 17)
+    ns = int(np.prod(shape[1:]))
+    closed = (rng.uniform(size=(ndim, ns)) < 0.15).astype(np.uint8)
+    C = inputs.random_unitary(2 * ndim, rng)
+    psi0 = inputs.random_state(shape, seed=25)
+    T = 19
+    for adj in (False, True):
+        want = oracle.evolve(psi0, C, T, shift=shift, bc=bc, closed=closed, adjoint=adj)
+        if ndim == 1:
+            w = qw.Walk((shape[1],), prec=prec, shift=shift, bc=bc)
+        else:
+            w = qw.Walk((shape[2], shape[1]), prec=prec, shift=shift, bc=bc)
+        w.set_coin(C).set_links(closed).set_state(psi0)
+        (w.step_adjoint if adj else w.step)(T)
+        assert maxabs(w.state(), want) < amp_tol(prec, T)
+        w.close()
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 6])
+def test_tiny_torus(qw, L):
+    rng = np.random.default_rng(L)
+    C = inputs.random_unitary(4, rng)
+    psi0 = inputs.random_state((4, L, L), seed=L)
+    want = oracle.evolve(psi0, C, 9)
+    got, _, _ = gpu_run(qw, psi0, C, 9, "f64")
+    assert maxabs(got, want) < 1e-12
