@@ -307,6 +307,30 @@ def run_gpu(args, rank, world, local):
                "frac_of_8000": 32.0 * N_SITES / k1_s / 1e9 / 8000.0}
     w.set_plan(K, tile)
 
+    # the torus: the fused 2D step (k = 1) on the 8192^2 lattice, against the HBM roof
+    torus = {}
+    if rank == 0 and not args.skip_forms:
+        from paper_1003_3779_gb300 import inputs as _in
+        L = 8192
+        g = torch.Generator(device=f"cuda:{local}").manual_seed(2)
+        z = torch.randn((4, L, L), dtype=torch.complex64, device=f"cuda:{local}", generator=g)
+        z /= z.abs().pow(2).sum().sqrt()
+        for name, coin, shift in (("grover_moving", _in.grover(), 0), ("hh_moving", _in.hadamard2(), 0),
+                                  ("grover_flipflop", _in.grover(), 1)):
+            w2 = qw.Walk((L, L), prec="f32", shift=shift).set_coin(coin).set_state(z)
+            w2.step(8)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            w2.step(64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts = a.elapsed_time(b) / 1e3 / 64
+            gbs = 64.0 * L * L / ts / 1e9
+            torus[name] = {"site_coin_updates_per_s": 4.0 * L * L / ts, "ms_per_step": ts * 1e3,
+                           "hbm_gbs": gbs, "frac_of_measured": gbs / hbm_gbs, "frac_of_8000": gbs / 8000.0}
+            w2.close()
+        del z
+
     # accuracy and the other precision forms on the same input (rank 0 only)
     forms, accuracy = {}, {}
     if rank == 0 and not args.skip_forms:
@@ -374,6 +398,7 @@ def run_gpu(args, rank, world, local):
         "value": value, "elapsed": tmax, "norm": norm, "roofline": roof, "roofline_k1": roof_k1,
         "forms": forms, "accuracy": accuracy, "e2e": e2e, "clocks": clk.summary(), "tune": tune,
         "K": K, "tile": tile, "launches": args.steps * (launches_step + 2), "dist": dist,
+        "torus": torus,
     }
 
 
@@ -428,7 +453,8 @@ def main():
                    "step": "set_state (device copy) + T=4096 walk steps + marginals/norm"},
         "clocks": r["clocks"], "e2e": r["e2e"], "gpu_launches": r["launches"],
         "roofline": r["roofline"], "roofline_k1": r["roofline_k1"], "cpu_baseline": cpu,
-        "accuracy": r["accuracy"], "forms": r["forms"], "norm": r["norm"], "autotune": r["tune"],
+        "accuracy": r["accuracy"], "forms": r["forms"], "torus_8192_k1": r["torus"],
+        "norm": r["norm"], "autotune": r["tune"],
     }
     print(json.dumps(out))
 

@@ -56,11 +56,11 @@ __device__ __forceinline__ void store_run(View v, int c, int64_t s, int j0, int 
     if (j0 >= lo && j0 + R <= hi && (s % S::VEC) == 0) {
 #pragma unroll
         for (int j = 0; j < R; j += S::VEC) S::stv(v, c, s + j, &a[j]);
-    } else {
+    } else if (j0 + R > lo && j0 < hi) {   // a lane straddling an end of the output range
 #pragma unroll
         for (int j = 0; j < R; ++j)
             if (j0 + j >= lo && j0 + j < hi) S::st(v, c, s + j, a[j]);
-    }
+    }                                      // lanes holding only halo sites store nothing
 }
 
 // phi = C psi for one site, d = 2.
@@ -109,7 +109,17 @@ __device__ __forceinline__ void coin2_adj(const CoinP<R> &cp, const Cx<R> *m, Cx
     }
 }
 
-// W = 32R - 2K output sites per warp; nwarps = ceil(n / W).
+// Tile origin of a warp whose first output site is out0: out0 - K rounded down
+// to the vector width, so that every lane's run starts on a 16-byte boundary
+// whatever K is.  W (outputs per warp) is a multiple of VEC with
+// 32R >= W + 2K + VEC - 1, so the tile still covers the light cone.
+template <int VEC>
+__device__ __forceinline__ int64_t tile_origin(int64_t out0, int K) {
+    const int64_t t = out0 - K;
+    return t >= 0 ? t - t % VEC : -((-t + VEC - 1) / VEC) * VEC;
+}
+
+// W output sites per warp (see tile_origin); nwarps = ceil(n / W).
 template <int P, int R, int CK, int FF, int ADJ>
 __global__ void __launch_bounds__(128)
 k_step1d(View in, View out, int64_t n, int K, int64_t W, int64_t nwarps,
@@ -124,7 +134,9 @@ k_step1d(View in, View out, int64_t n, int K, int64_t W, int64_t nwarps,
     const int64_t out0 = warp * W;
     const int wthis = (int)min(W, n - out0);
     const int j0 = lane * R;
-    const int64_t s = out0 - K + j0;
+    const int64_t ts = tile_origin<St<P>::VEC>(out0, K);
+    const int lo = (int)(out0 - ts);   // first output's tile position, in [K, K + VEC)
+    const int64_t s = ts + j0;
 
     C a0[R], a1[R];
     load_run<P, R>(in, 0, s, n, a0);
@@ -206,8 +218,118 @@ k_step1d(View in, View out, int64_t n, int K, int64_t W, int64_t nwarps,
 #pragma unroll
         for (int i = 0; i < R; ++i) a1[i] = rmul(post1, a1[i]);
     }
-    store_run<P, R>(out, 0, s, j0, K, K + wthis, a0);
-    store_run<P, R>(out, 1, s, j0, K, K + wthis, a1);
+    store_run<P, R>(out, 0, s, j0, lo, lo + wthis, a0);
+    store_run<P, R>(out, 1, s, j0, lo, lo + wthis, a1);
+}
+
+// ---------------------------------------------------------------- k = 1
+// One step per launch, streaming: each lane owns one 16-byte vector per plane
+// (VEC sites), so every warp load / store is one fully coalesced 512-byte
+// access.  The value that enters a lane from its neighbour comes by shuffle;
+// at the warp edges lane 0 and lane 31 evaluate the one site outside the
+// warp's range themselves (periodic), so nothing is recomputed elsewhere.
+template <int P, int CK, int FF, int ADJ>
+__device__ void step1d_site(View in, View out, int64_t n, int64_t x, const CoinP<typename St<P>::real> &cp,
+                            const Cx<typename St<P>::real> *coins, typename St<P>::real pre0,
+                            typename St<P>::real pre1, typename St<P>::real post0,
+                            typename St<P>::real post1) {
+    using real = typename St<P>::real;
+    using S = St<P>;
+    using C = Cx<real>;
+    const int64_t xm = x == 0 ? n - 1 : x - 1, xp = x + 1 == n ? 0 : x + 1;
+    C r0, r1;
+    if (!ADJ) {
+        // coin at x+1 (its coin-0 output moves to x) and at x-1 (coin 1 moves to x)
+        C u0 = rmul(pre0, S::ld(in, 0, xp)), u1 = rmul(pre1, S::ld(in, 1, xp)), p0, p1;
+        coin2<CK>(cp, coins + 4 * xp, u0, u1, p0, p1);
+        C v0 = rmul(pre0, S::ld(in, 0, xm)), v1 = rmul(pre1, S::ld(in, 1, xm)), q0, q1;
+        coin2<CK>(cp, coins + 4 * xm, v0, v1, q0, q1);
+        r0 = FF ? q1 : p0;
+        r1 = FF ? p0 : q1;
+    } else {
+        C b0, b1;
+        if (!FF) { b0 = rmul(pre0, S::ld(in, 0, xm)); b1 = rmul(pre1, S::ld(in, 1, xp)); }
+        else { b0 = rmul(pre1, S::ld(in, 1, xm)); b1 = rmul(pre0, S::ld(in, 0, xp)); }
+        coin2_adj<CK>(cp, coins + 4 * x, b0, b1, r0, r1);
+    }
+    S::st(out, 0, x, rmul(post0, r0));
+    S::st(out, 1, x, rmul(post1, r1));
+}
+
+template <int P, int CK, int FF, int ADJ>
+__global__ void __launch_bounds__(256)
+k_step1d_k1(View in, View out, int64_t n, int64_t nwarps, CoinP<typename St<P>::real> cp,
+            const Cx<typename St<P>::real> *__restrict__ coins, typename St<P>::real pre0,
+            typename St<P>::real pre1, typename St<P>::real post0, typename St<P>::real post1) {
+    using real = typename St<P>::real;
+    using S = St<P>;
+    using C = Cx<real>;
+    constexpr int R = S::VEC;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (warp >= nwarps) return;  // uniform per warp
+    const int64_t x0 = warp * (32 * R);
+    const int64_t xs = x0 + lane * R;
+    if (x0 + 32 * R > n) {       // ragged tail (uniform per warp): per-site pull
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+            if (xs + i < n) step1d_site<P, CK, FF, ADJ>(in, out, n, xs + i, cp, coins, pre0, pre1, post0, post1);
+        return;
+    }
+    C a0[R], a1[R];
+    S::ldv(in, 0, xs, a0);
+    S::ldv(in, 1, xs, a1);
+#pragma unroll
+    for (int i = 0; i < R; ++i) { a0[i] = rmul(pre0, a0[i]); a1[i] = rmul(pre1, a1[i]); }
+    const int64_t xl = x0 == 0 ? n - 1 : x0 - 1;        // site left of the warp
+    const int64_t xr = (x0 + 32 * R == n) ? 0 : x0 + 32 * R;  // site right of the warp
+    C r0[R], r1[R];
+    if (!ADJ) {
+        C p0[R], p1[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) coin2<CK>(cp, coins + 4 * (xs + i), a0[i], a1[i], p0[i], p1[i]);
+        C halo = czero<real>();
+        if (lane == 0 || lane == 31) {
+            const int64_t xh = lane == 0 ? xl : xr;
+            C h0 = rmul(pre0, S::ld(in, 0, xh)), h1 = rmul(pre1, S::ld(in, 1, xh)), q0, q1;
+            coin2<CK>(cp, coins + 4 * xh, h0, h1, q0, q1);
+            halo = lane == 0 ? q1 : q0;
+        }
+        C from_right = shfl_down(p0[0], 1);
+        C from_left = shfl_up(p1[R - 1], 1);
+        if (lane == 31) from_right = halo;
+        if (lane == 0) from_left = halo;
+        // coin 0 arrives from x+1, coin 1 from x-1; flip-flop swaps the planes
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const C in0 = (i == R - 1) ? from_right : p0[i + 1];
+            const C in1 = (i == 0) ? from_left : p1[i - 1];
+            r0[i] = FF ? in1 : in0;
+            r1[i] = FF ? in0 : in1;
+        }
+    } else {
+        // S^dagger: moving b0(x) = psi0(x-1), b1(x) = psi1(x+1); flip-flop b0(x) = psi1(x-1), b1(x) = psi0(x+1)
+        C lsrc[R], rsrc[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) { lsrc[i] = FF ? a1[i] : a0[i]; rsrc[i] = FF ? a0[i] : a1[i]; }
+        C halo = czero<real>();
+        if (lane == 0) halo = FF ? rmul(pre1, S::ld(in, 1, xl)) : rmul(pre0, S::ld(in, 0, xl));
+        if (lane == 31) halo = FF ? rmul(pre0, S::ld(in, 0, xr)) : rmul(pre1, S::ld(in, 1, xr));
+        C from_left = shfl_up(lsrc[R - 1], 1);
+        C from_right = shfl_down(rsrc[0], 1);
+        if (lane == 0) from_left = halo;
+        if (lane == 31) from_right = halo;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const C b0 = (i == 0) ? from_left : lsrc[i - 1];
+            const C b1 = (i == R - 1) ? from_right : rsrc[i + 1];
+            coin2_adj<CK>(cp, coins + 4 * (xs + i), b0, b1, r0[i], r1[i]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) { r0[i] = rmul(post0, r0[i]); r1[i] = rmul(post1, r1[i]); }
+    S::stv(out, 0, xs, r0);
+    S::stv(out, 1, xs, r1);
 }
 
 }  // namespace qw

@@ -21,9 +21,41 @@ template <> struct Tiles1D<P_COMP> { static constexpr int A = 4, B = 8, DEF = 4;
 template <int P> struct Tile2D { static constexpr int R = 32 / St<P>::SLOT_BYTES < 1 ? 1 : 32 / St<P>::SLOT_BYTES; };
 template <> struct Tile2D<P_COMP> { static constexpr int R = 4; };
 
+template <int P, int CK, int FF, int ADJ>
+static void go1d_k1(const Step1DArgs &a, const CoinP<typename St<P>::real> &cp, cudaStream_t s) {
+    using real = typename St<P>::real;
+    const int64_t nwarps = (a.n + 32 * St<P>::VEC - 1) / (32 * St<P>::VEC);
+    const int64_t blocks = (nwarps + 7) / 8;
+    k_step1d_k1<P, CK, FF, ADJ><<<(unsigned)blocks, 256, 0, s>>>(
+        a.in, a.out, a.n, nwarps, cp, static_cast<const Cx<real> *>(a.coins),
+        real_from_double<real>(a.pre0), real_from_double<real>(a.pre1),
+        real_from_double<real>(a.post0), real_from_double<real>(a.post1));
+}
+
+template <int P, int ADJ>
+static bool go1d_k1_kind(const Step1DArgs &a, const CoinP<typename St<P>::real> &cp, cudaStream_t s) {
+    const bool ff = a.shift == QW_SHIFT_FLIPFLOP;
+    switch (a.kind) {
+        case CK_REAL: ff ? go1d_k1<P, CK_REAL, 1, ADJ>(a, cp, s) : go1d_k1<P, CK_REAL, 0, ADJ>(a, cp, s); return true;
+        case CK_COMPLEX: ff ? go1d_k1<P, CK_COMPLEX, 1, ADJ>(a, cp, s) : go1d_k1<P, CK_COMPLEX, 0, ADJ>(a, cp, s); return true;
+        case CK_PERSITE: ff ? go1d_k1<P, CK_PERSITE, 1, ADJ>(a, cp, s) : go1d_k1<P, CK_PERSITE, 0, ADJ>(a, cp, s); return true;
+        case CK_SIGN_P: if (ff) return false; go1d_k1<P, CK_SIGN_P, 0, ADJ>(a, cp, s); return true;
+        case CK_SIGN_M: if (ff) return false; go1d_k1<P, CK_SIGN_M, 0, ADJ>(a, cp, s); return true;
+        default: return false;
+    }
+}
+
+// Outputs per warp of the temporal-blocking kernel: a multiple of VEC with
+// 32R >= W + 2K + VEC - 1 (the tile origin is rounded down to VEC).
+template <int P>
+inline int64_t outputs_per_warp(int R, int K) {
+    constexpr int V = St<P>::VEC;
+    return (32LL * R - 2LL * K - (V - 1)) / V * V;
+}
+
 template <int P, int R, int CK, int FF, int ADJ>
 static void go1d(const Step1DArgs &a, const CoinP<typename St<P>::real> &cp, cudaStream_t s) {
-    const int64_t W = 32LL * R - 2LL * a.K;
+    const int64_t W = outputs_per_warp<P>(R, a.K);
     const int64_t nwarps = (a.n + W - 1) / W;
     const int64_t blocks = (nwarps + 3) / 4;
     k_step1d<P, R, CK, FF, ADJ><<<(unsigned)blocks, 128, 0, s>>>(
@@ -63,6 +95,10 @@ cudaError_t step1d_t(const Step1DArgs &a0, const void *coinp, int adj, cudaStrea
     a.tile = tile1d_effective<P>(a.tile, a.kind, adj);
     if (a.K < 1 || a.K > max_k_1d(a.tile)) return cudaErrorInvalidValue;
     const bool ff = a.shift == QW_SHIFT_FLIPFLOP;
+    if (a.K == 1) {   // one step per launch: the streaming kernel
+        const bool ok = adj ? go1d_k1_kind<P, 1>(a, cp, s) : go1d_k1_kind<P, 0>(a, cp, s);
+        return ok ? cudaGetLastError() : cudaErrorInvalidValue;
+    }
     if (!adj) {
         if (a.kind == CK_PERSITE) {
             ff ? go1d<P, T::DEF, CK_PERSITE, 1, 0>(a, cp, s) : go1d<P, T::DEF, CK_PERSITE, 0, 0>(a, cp, s);
