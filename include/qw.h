@@ -179,6 +179,34 @@ qw_status qw_synchronize(qw_walk *w);
 qw_status qw_backward(qw_walk *w, const int64_t rect[4], int64_t T, int64_t K,
                       double *loss_out, double *grad_phi, int on_device);
 
+/* Coin marginals and norm of a state the caller owns, without allocating any
+ * memory: the same P(v) = sum_c |psi(v,c)|^2 and fixed-order double norm as
+ * qw_probabilities, for callers that cannot call cudaMalloc -- a thread that
+ * runs while another thread holds a global-mode stream capture (cudaMalloc
+ * fails then), an application whose own allocator has already reserved the
+ * device memory, or a latency-critical path that cannot take cudaMalloc's
+ * implicit device synchronisation.  The paper has no counterpart.
+ *
+ * amp: device pointer, coin_dim dense coin-major planes of nsites complex
+ * numbers (QW_C64 or QW_C128), element-aligned.  P_out: device pointer to
+ * nsites values of pdtype, or NULL.  norm_out: device pointer to one double,
+ * or NULL.  Everything is enqueued on cuda_stream; nothing synchronises.
+ *
+ * Scratch: one double per 8192 sites in a fixed array inside the library
+ * (16384 doubles = 128 KiB, held by every GPU that loads the library until the
+ * process exits), so nsites is limited to 16384 * 8192 = 2^27; larger sizes,
+ * a NULL amp, nsites < 1, a coin_dim other than 2 or 4, or an unknown dtype
+ * return QW_EINVAL before anything is launched.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress, with the device
+ * current); make that first call before any stream capture.  All calls share
+ * the array: each call overwrites the slots it uses, so nothing needs
+ * clearing, but two calls that overlap on the GPU (different streams, or
+ * different host threads) race on it and must be ordered by the caller.
+ * Returns QW_ECUDA if the lookup or a launch fails. */
+qw_status qw_probabilities_noalloc(const void *amp, qw_cdtype dtype, int coin_dim, int64_t nsites,
+                                   void *P_out, qw_rdtype pdtype, double *norm_out,
+                                   void *cuda_stream);
+
 /* ---------------------------------------------------------------- batches */
 
 /* A batch of independent 1D walks on cycles (Sec. 2.2), walk i with N[i]

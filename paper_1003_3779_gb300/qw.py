@@ -75,6 +75,7 @@ def lib():
         "qw_batch_last_error": (ctypes.c_char_p, [P]),
         "qw_version": (ctypes.c_char_p, []),
         "qw_debug_bounded_wait": (I, [I64, P]),
+        "qw_probabilities_noalloc": (I, [P, I, I, I64, P, I, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -233,6 +234,20 @@ def qw_backward(h, rect, T, K, grad_out):
     _check(lib().qw_backward(h, _ptr(r), int(T), int(K), ctypes.byref(loss), _ptr(grad_out),
                              _on_device(grad_out)), h)
     return loss.value
+
+
+def qw_probabilities_noalloc(amp, P_out=None, norm_out=None, stream=None):
+    """Marginals and norm of a caller-owned device state without any library
+    allocation (see include/qw.h).  amp: torch complex64/complex128 tensor of
+    shape (d, ...) on the GPU; P_out: float32/float64 device tensor or None;
+    norm_out: one-element float64 device tensor or None.  Returns the status."""
+    import torch
+    d = int(amp.shape[0])
+    ns = int(amp[0].numel())
+    dt = C64 if amp.dtype == torch.complex64 else C128
+    pd = R32 if (P_out is not None and P_out.dtype == torch.float32) else R64
+    return lib().qw_probabilities_noalloc(_ptr(amp), dt, d, ns, _ptr(P_out), pd, _ptr(norm_out),
+                                          stream if stream is not None else _stream())
 
 
 def qw_debug_bounded_wait(spins, stream=None):
