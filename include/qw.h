@@ -213,8 +213,12 @@ qw_status qw_probabilities_noalloc(const void *amp, qw_cdtype dtype, int coin_di
  * sites, T[i] steps, its own 2x2 coin (coins + 8*i: row-major complex), and the
  * localised initial state |x0[i]> (x) (coin_state[0]|0> + coin_state[1]|1>)
  * (coin_state: 2 complex = 4 doubles).  prec: QW_F32 or QW_F32_BF16STORE
- * (state storage; arithmetic is float).  All arrays are host pointers.
- * Device memory: the final states of all walks and their probabilities. */
+ * (state storage; arithmetic is float), anything else QW_EUNSUPPORTED.  All
+ * arrays are host pointers; QW_EINVAL for N < 1, T < 0 or x0 outside [0, N).
+ * Device memory: two state buffers for all walks (ping-pong), their
+ * probabilities (float) and norms.  One CTA advances one walk at a time; a
+ * walk's tiles outside the light cone [x0 - t, x0 + t] of its localised start
+ * are skipped (exact zeros). */
 qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T,
                           const double *coins, const int64_t *x0,
                           const double *coin_state, qw_precision prec,
@@ -225,6 +229,15 @@ qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T,
  * call) and compute each walk's probabilities.  Repeated calls start again
  * from the initial states. */
 qw_status qw_batch_step(qw_batch *b);
+
+/* Temporal depth k (steps per round, 1..128) of the batched kernel; the tile
+ * is fixed at 16 sites per lane.  Changing k re-captures the graph. */
+qw_status qw_batch_set_plan(qw_batch *b, int depth_k);
+qw_status qw_batch_get_plan(const qw_batch *b, int *depth_k, int *tile);
+
+/* Time the batch for k in {8, ..., 128} (each timing runs the whole batch from
+ * its initial states) and keep the fastest; report as for qw_autotune. */
+qw_status qw_batch_autotune(qw_batch *b, char *report, size_t report_len);
 
 /* Probabilities of all walks, concatenated in walk order (walk i starts at
  * sum_{j<i} N[j]), float, host or device; norms (host, may be NULL): nwalks

@@ -119,19 +119,17 @@ __device__ __forceinline__ int64_t tile_origin(int64_t out0, int K) {
     return t >= 0 ? t - t % VEC : -((-t + VEC - 1) / VEC) * VEC;
 }
 
-// W output sites per warp (see tile_origin); nwarps = ceil(n / W).
+// One warp tile: K steps on the 32R sites around outputs [tile*W, tile*W + W).
+// Called by the cycle kernel below and by the batched kernel (one walk per CTA).
 template <int P, int R, int CK, int FF, int ADJ>
-__global__ void __launch_bounds__(128)
-k_step1d(View in, View out, int64_t n, int K, int64_t W, int64_t nwarps,
-         CoinP<typename St<P>::real> cp, const Cx<typename St<P>::real> *__restrict__ coins,
-         typename St<P>::real pre0, typename St<P>::real pre1,
-         typename St<P>::real post0, typename St<P>::real post1) {
+__device__ __forceinline__ void tb_tile(View in, View out, int64_t n, int K, int64_t W, int64_t tile, int lane,
+                                        const CoinP<typename St<P>::real> &cp,
+                                        const Cx<typename St<P>::real> *__restrict__ coins,
+                                        typename St<P>::real pre0, typename St<P>::real pre1,
+                                        typename St<P>::real post0, typename St<P>::real post1) {
     using real = typename St<P>::real;
     using C = Cx<real>;
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (warp >= nwarps) return;  // uniform per warp
-    const int64_t out0 = warp * W;
+    const int64_t out0 = tile * W;
     const int wthis = (int)min(W, n - out0);
     const int j0 = lane * R;
     const int64_t ts = tile_origin<St<P>::VEC>(out0, K);
@@ -220,6 +218,19 @@ k_step1d(View in, View out, int64_t n, int K, int64_t W, int64_t nwarps,
     }
     store_run<P, R>(out, 0, s, j0, lo, lo + wthis, a0);
     store_run<P, R>(out, 1, s, j0, lo, lo + wthis, a1);
+}
+
+// W output sites per warp (see tile_origin); nwarps = ceil(n / W).
+template <int P, int R, int CK, int FF, int ADJ>
+__global__ void __launch_bounds__(128)
+k_step1d(View in, View out, int64_t n, int K, int64_t W, int64_t nwarps,
+         CoinP<typename St<P>::real> cp, const Cx<typename St<P>::real> *__restrict__ coins,
+         typename St<P>::real pre0, typename St<P>::real pre1,
+         typename St<P>::real post0, typename St<P>::real post1) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (warp >= nwarps) return;  // uniform per warp
+    tb_tile<P, R, CK, FF, ADJ>(in, out, n, K, W, warp, lane, cp, coins, pre0, pre1, post0, post1);
 }
 
 // ---------------------------------------------------------------- k = 1

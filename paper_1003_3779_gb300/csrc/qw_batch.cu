@@ -1,0 +1,419 @@
+// qw_batch.cu -- many independent walks on cycles in one persistent launch.
+//
+// Each walk is the 1D walk of Sec. 2.2 (cycle Z_N, coin dim 2, U = S (I (x) C)
+// of Sec. 2.1) with its own N, T and 2x2 coin, started localised at x0.  One
+// CTA owns one walk at a time: it pops the next walk from a global counter
+// (walks sorted by N*T, longest first), zeroes the walk's two state buffers,
+// places the initial amplitude, and advances the walk k steps per round with
+// the same warp register-tile kernel as the single cycle (tb_tile), its four
+// warps sharing the tiles of the walk and meeting at a __syncthreads between
+// rounds.  The walk's state ping-pongs between two global buffers; a walk of
+// at most 65536 sites is 1 MiB per buffer in FP32 (0.5 MiB in bfloat16), so it
+// mostly stays in L2 while its CTA works on it.
+//
+// Light cone (Sec. 3, the "line" computation window): after t steps from a
+// single site x0 the state is zero outside [x0 - t, x0 + t].  A tile whose
+// outputs all lie outside the cone of the current round is skipped; its
+// buffer region is still the zero written at the start.
+//
+// At the end of its walk the CTA writes P(x) = |psi0|^2 + |psi1|^2 (float) and
+// the walk's norm (double, fixed order) to the batch outputs.  There are no
+// waits other than __syncthreads: nothing spins.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "qw_handle.h"
+#include "k_step1d.cuh"
+
+namespace qw {
+
+struct WalkDesc {
+    int64_t n, T, x0;
+    int64_t base;    // first site slot of the walk in each state buffer (plane 0; plane 1 at +pitch)
+    int64_t pitch;   // sites per plane, a multiple of 64
+    int64_t poff;    // first index of the walk in the concatenated probabilities
+    float c[8];      // coin, row-major complex (re, im)
+    double alpha;    // sqrt(|C_f|_F^2 / 2) of the float-rounded coin (norm-drift factor per step)
+};
+
+struct BatchArgs {
+    const WalkDesc *walks;
+    const int *order;
+    int nwalks;
+    void *buf0, *buf1;
+    float *P;
+    double *norms;
+    int *counter;
+    int *final_buf;
+    int K;
+    float cs[4];     // coin state at x0: (re, im) of coin 0 and coin 1
+};
+
+constexpr int BATCH_THREADS = 128;
+constexpr int BATCH_R = 16;
+
+// Does the tile output range [a, b) meet the circular interval [x0 - r, x0 + r] (mod n)?
+__device__ __forceinline__ bool meets_cone(int64_t a, int64_t b, int64_t x0, int64_t r, int64_t n) {
+    int64_t lo = x0 - r, hi = x0 + r + 1;   // half-open, 2r + 1 < n
+    if (lo < 0) return (a < hi) || (b > lo + n);
+    if (hi > n) return (b > lo) || (a < hi - n);
+    return a < hi && b > lo;
+}
+
+template <int P, int CK>
+__global__ void __launch_bounds__(BATCH_THREADS)
+k_batch(BatchArgs a) {
+    using S = St<P>;
+    constexpr int R = BATCH_R;
+    constexpr int VEC = S::VEC;
+    __shared__ int s_q;
+    __shared__ double s_red[BATCH_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_q = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int q = s_q;
+        if (q >= a.nwalks) return;
+        const int w = a.order[q];
+        const WalkDesc d = a.walks[w];
+        View in{static_cast<char *>(a.buf0) + d.base * S::SLOT_BYTES, d.pitch, 2};
+        View out{static_cast<char *>(a.buf1) + d.base * S::SLOT_BYTES, d.pitch, 2};
+
+        // zero both buffers of this walk, then place the start
+        {
+            const int64_t nvec = 2 * d.pitch * S::SLOT_BYTES / 16;
+            uint4 z = make_uint4(0, 0, 0, 0);
+            for (int64_t i = threadIdx.x; i < nvec; i += blockDim.x) {
+                reinterpret_cast<uint4 *>(in.p)[i] = z;
+                reinterpret_cast<uint4 *>(out.p)[i] = z;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            S::st(in, 0, d.x0, Cx<float>{a.cs[0], a.cs[1]});
+            S::st(in, 1, d.x0, Cx<float>{a.cs[2], a.cs[3]});
+        }
+        __syncthreads();
+
+        CoinP<float> cp;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) { cp.re[e] = d.c[2 * e]; cp.im[e] = d.c[2 * e + 1]; }
+        double fb = 1.0;   // error feedback of the per-round drift factor
+        int cur = 0;
+        for (int64_t t0 = 0; t0 < d.T; t0 += a.K) {
+            const int k = (int)min((int64_t)a.K, d.T - t0);
+            const int64_t W = (32LL * R - 2LL * k - (VEC - 1)) / VEC * VEC;
+            const int64_t ntiles = (d.n + W - 1) / W;
+            const int64_t r = t0 + k;
+            const bool all = 2 * r + 1 >= d.n;
+            const double ideal = pow(d.alpha, -(double)k);
+            const float g = (float)(ideal / fb);
+            fb *= (double)g / ideal;
+            for (int64_t tile = wid; tile < ntiles; tile += nw) {
+                const int64_t o0 = tile * W, o1 = min(o0 + W, d.n);
+                if (!all && !meets_cone(o0, o1, d.x0, r, d.n)) continue;
+                tb_tile<P, R, CK, 0, 0>(in, out, d.n, k, W, tile, lane, cp, nullptr, 1.f, 1.f, g, g);
+            }
+            __syncthreads();
+            View t = in; in = out; out = t;
+            cur ^= 1;
+        }
+
+        // marginals and norm of the final state
+        double acc = 0.0;
+        for (int64_t x = threadIdx.x; x < d.n; x += blockDim.x) {
+            const double p = norm2d(S::ld(in, 0, x)) + norm2d(S::ld(in, 1, x));
+            a.P[d.poff + x] = (float)p;
+            acc += p;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) s_red[wid] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int i = 0; i < nw; ++i) tot += s_red[i];
+            a.norms[w] = tot;
+            a.final_buf[w] = cur;
+        }
+    }
+}
+
+}  // namespace qw
+
+using namespace qw;
+
+struct qw_batch {
+    int nwalks = 0;
+    int prec = QW_F32;
+    int kind = CK_REAL;
+    cudaStream_t stream = nullptr;      // caller's stream
+    cudaStream_t cap = nullptr;         // private stream the graph is captured on
+    std::vector<WalkDesc> walks;
+    std::vector<int> order;
+    int64_t total_sites = 0, total_slots = 0;
+    size_t buf_bytes = 0;
+    void *buf[2] = {nullptr, nullptr};
+    WalkDesc *walks_dev = nullptr;
+    int *order_dev = nullptr;
+    float *P_dev = nullptr;
+    double *norms_dev = nullptr;
+    int *counter = nullptr;
+    int *final_dev = nullptr;
+    int K = 32;
+    int grid = 0;
+    float cs[4] = {0, 0, 0, 0};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool ran = false;
+    std::string err;
+};
+
+static qw_status batch_fail(qw_batch *b, qw_status st, const std::string &m) {
+    if (b) b->err = m;
+    return st;
+}
+
+static qw_status batch_cuda(qw_batch *b, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    (void)cudaGetLastError();
+    return batch_fail(b, e == cudaErrorMemoryAllocation ? QW_ENOMEM : QW_ECUDA, m);
+}
+
+static cudaError_t batch_launch(qw_batch *b, cudaStream_t s) {
+    BatchArgs a{};
+    a.walks = b->walks_dev; a.order = b->order_dev; a.nwalks = b->nwalks;
+    a.buf0 = b->buf[0]; a.buf1 = b->buf[1]; a.P = b->P_dev; a.norms = b->norms_dev;
+    a.counter = b->counter; a.final_buf = b->final_dev; a.K = b->K;
+    std::memcpy(a.cs, b->cs, sizeof a.cs);
+    cudaError_t e = cudaMemsetAsync(b->counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    if (b->prec == QW_F32_BF16STORE) {
+        if (b->kind == CK_REAL) k_batch<P_BF16, CK_REAL><<<b->grid, BATCH_THREADS, 0, s>>>(a);
+        else k_batch<P_BF16, CK_COMPLEX><<<b->grid, BATCH_THREADS, 0, s>>>(a);
+    } else {
+        if (b->kind == CK_REAL) k_batch<P_F32, CK_REAL><<<b->grid, BATCH_THREADS, 0, s>>>(a);
+        else k_batch<P_F32, CK_COMPLEX><<<b->grid, BATCH_THREADS, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+static void drop_graph(qw_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+extern "C" {
+
+qw_status qw_batch_destroy(qw_batch *b) {
+    if (!b) return QW_OK;
+    cudaStreamSynchronize(b->stream);
+    if (b->cap) cudaStreamSynchronize(b->cap);
+    drop_graph(b);
+    cudaFree(b->buf[0]);
+    cudaFree(b->buf[1]);
+    cudaFree(b->walks_dev);
+    cudaFree(b->order_dev);
+    cudaFree(b->P_dev);
+    cudaFree(b->norms_dev);
+    cudaFree(b->counter);
+    cudaFree(b->final_dev);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return QW_OK;
+}
+
+const char *qw_batch_last_error(const qw_batch *b) { return b ? b->err.c_str() : "null handle"; }
+
+qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T, const double *coins,
+                          const int64_t *x0, const double *coin_state, qw_precision prec,
+                          void *cuda_stream, qw_batch **out) {
+    if (!out) return QW_EINVAL;
+    *out = nullptr;
+    if (nwalks < 1 || !N || !T || !coins || !x0 || !coin_state) return QW_EINVAL;
+    if (prec != QW_F32 && prec != QW_F32_BF16STORE) return QW_EUNSUPPORTED;
+    for (int i = 0; i < nwalks; ++i)
+        if (N[i] < 1 || N[i] > (int64_t(1) << 31) || T[i] < 0 || x0[i] < 0 || x0[i] >= N[i]) return QW_EINVAL;
+
+    qw_batch *b = new (std::nothrow) qw_batch();
+    if (!b) return QW_ENOMEM;
+    b->nwalks = nwalks;
+    b->prec = prec;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    for (int i = 0; i < 4; ++i) b->cs[i] = (float)coin_state[i];
+    b->walks.resize(nwalks);
+    bool real = true;
+    int64_t base = 0, poff = 0;
+    for (int i = 0; i < nwalks; ++i) {
+        WalkDesc &d = b->walks[i];
+        d.n = N[i]; d.T = T[i]; d.x0 = x0[i];
+        d.pitch = (N[i] + 63) / 64 * 64;
+        d.base = base;
+        d.poff = poff;
+        base += 2 * d.pitch;
+        poff += N[i];
+        double fro = 0.0;
+        for (int e = 0; e < 8; ++e) {
+            d.c[e] = (float)coins[8 * i + e];
+            fro += (double)d.c[e] * d.c[e];
+            if (e % 2 == 1 && coins[8 * i + e] != 0.0) real = false;
+        }
+        const double alpha = std::sqrt(fro / 2.0);
+        d.alpha = std::fabs(alpha - 1.0) <= 1e-5 ? alpha : 1.0;
+    }
+    b->kind = real ? CK_REAL : CK_COMPLEX;
+    b->total_slots = base;
+    b->total_sites = poff;
+    b->order.resize(nwalks);
+    std::iota(b->order.begin(), b->order.end(), 0);
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int p, int q) {
+        return (double)N[p] * (double)T[p] > (double)N[q] * (double)T[q];
+    });
+    const int slot = prec == QW_F32_BF16STORE ? 4 : 8;
+    b->buf_bytes = (size_t)base * slot;
+
+    cudaError_t e = cudaSuccess;
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, prec == QW_F32_BF16STORE ? (const void *)k_batch<P_BF16, CK_REAL> : (const void *)k_batch<P_F32, CK_REAL>,
+            BATCH_THREADS, 0);
+    if (e == cudaSuccess) e = dev_alloc(&b->buf[0], b->buf_bytes);
+    if (e == cudaSuccess) e = dev_alloc(&b->buf[1], b->buf_bytes);
+    if (e == cudaSuccess) e = dev_alloc((void **)&b->walks_dev, sizeof(WalkDesc) * nwalks);
+    if (e == cudaSuccess) e = dev_alloc((void **)&b->order_dev, sizeof(int) * nwalks);
+    if (e == cudaSuccess) e = dev_alloc((void **)&b->P_dev, sizeof(float) * (size_t)b->total_sites);
+    if (e == cudaSuccess) e = dev_alloc((void **)&b->norms_dev, sizeof(double) * nwalks);
+    if (e == cudaSuccess) e = dev_alloc((void **)&b->counter, sizeof(int));
+    if (e == cudaSuccess) e = dev_alloc((void **)&b->final_dev, sizeof(int) * nwalks);
+    if (e == cudaSuccess) e = cudaMemcpy(b->walks_dev, b->walks.data(), sizeof(WalkDesc) * nwalks, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->order_dev, b->order.data(), sizeof(int) * nwalks, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        qw_status st = e == cudaErrorMemoryAllocation ? QW_ENOMEM : QW_ECUDA;
+        (void)cudaGetLastError();
+        qw_batch_destroy(b);
+        return st;
+    }
+    b->grid = std::max(1, std::min(nwalks, sms * std::max(1, per_sm)));
+    *out = b;
+    return QW_OK;
+}
+
+qw_status qw_batch_step(qw_batch *b) {
+    if (!b) return QW_EINVAL;
+    cudaError_t e;
+    if (!b->exec) {
+        e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return batch_cuda(b, e, "graph capture begin");
+        cudaError_t le = batch_launch(b, b->cap);
+        e = cudaStreamEndCapture(b->cap, &b->graph);
+        if (le != cudaSuccess) { drop_graph(b); return batch_cuda(b, le, "batch launch (capture)"); }
+        if (e != cudaSuccess) { drop_graph(b); return batch_cuda(b, e, "graph capture end"); }
+        e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        if (e != cudaSuccess) { drop_graph(b); return batch_cuda(b, e, "graph instantiate"); }
+    }
+    e = cudaGraphLaunch(b->exec, b->stream);
+    if (e != cudaSuccess) return batch_cuda(b, e, "graph launch");
+    b->ran = true;
+    return QW_OK;
+}
+
+qw_status qw_batch_set_plan(qw_batch *b, int depth_k) {
+    if (!b) return QW_EINVAL;
+    if (depth_k < 1 || depth_k > 8 * BATCH_R) return batch_fail(b, QW_EINVAL, "k must be in [1, 128]");
+    if (depth_k != b->K) {
+        cudaStreamSynchronize(b->stream);
+        drop_graph(b);   // the captured launch carries k
+        b->K = depth_k;
+    }
+    return QW_OK;
+}
+
+qw_status qw_batch_get_plan(const qw_batch *b, int *depth_k, int *tile) {
+    if (!b || !depth_k || !tile) return QW_EINVAL;
+    *depth_k = b->K;
+    *tile = BATCH_R;
+    return QW_OK;
+}
+
+qw_status qw_batch_autotune(qw_batch *b, char *report, size_t report_len) {
+    if (!b) return QW_EINVAL;
+    const int ks[] = {8, 16, 24, 32, 48, 64, 96, 128};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_k = b->K;
+    cudaError_t e = cudaSuccess;
+    for (int k : ks) {
+        qw_status st = qw_batch_set_plan(b, k);
+        if (st != QW_OK) break;
+        if ((st = qw_batch_step(b)) != QW_OK) { e = cudaErrorUnknown; break; }   // capture + warm-up
+        cudaEventRecord(e0, b->stream);
+        qw_batch_step(b);
+        cudaEventRecord(e1, b->stream);
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_k = k; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e == cudaErrorUnknown ? QW_ECUDA : batch_cuda(b, e, "batch autotune");
+    qw_batch_set_plan(b, best_k);
+    if (report && report_len) {
+        std::snprintf(report, report_len, "{\"tuned\": true, \"k\": %d, \"tile\": %d, \"ms\": %.6g}", best_k, BATCH_R, best);
+    }
+    return QW_OK;
+}
+
+qw_status qw_batch_probabilities(qw_batch *b, float *P_concat, int on_device, double *norms) {
+    if (!b) return QW_EINVAL;
+    if (!b->ran) return batch_fail(b, QW_ESTATE, "qw_batch_step has not run");
+    cudaError_t e = cudaSuccess;
+    if (P_concat)
+        e = cudaMemcpyAsync(P_concat, b->P_dev, sizeof(float) * (size_t)b->total_sites,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess && norms)
+        e = cudaMemcpyAsync(norms, b->norms_dev, sizeof(double) * b->nwalks, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return e == cudaSuccess ? QW_OK : batch_cuda(b, e, "batch probabilities");
+}
+
+qw_status qw_batch_get_state(qw_batch *b, int walk, void *amp_out, qw_cdtype dtype) {
+    if (!b) return QW_EINVAL;
+    if (walk < 0 || walk >= b->nwalks || !amp_out || (dtype != QW_C128 && dtype != QW_C64))
+        return batch_fail(b, QW_EINVAL, "bad walk index, buffer or dtype");
+    if (!b->ran) return batch_fail(b, QW_ESTATE, "qw_batch_step has not run");
+    const WalkDesc &d = b->walks[walk];
+    int which = 0;
+    cudaError_t e = cudaMemcpyAsync(&which, b->final_dev + walk, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return batch_cuda(b, e, "batch state");
+    const int slot = b->prec == QW_F32_BF16STORE ? 4 : 8;
+    View v{static_cast<char *>(b->buf[which]) + d.base * slot, d.pitch, 2};
+    const size_t eb = dtype == QW_C128 ? 16 : 8;
+    void *tmp = nullptr;
+    e = dev_alloc(&tmp, 2 * (size_t)d.n * eb);
+    if (e != cudaSuccess) return batch_cuda(b, e, "batch state staging");
+    const int prec = b->prec == QW_F32_BF16STORE ? P_BF16 : P_F32;
+    for (int c = 0; c < 2 && e == cudaSuccess; ++c)
+        e = launch_export(prec, v, d.n, static_cast<char *>(tmp) + c * d.n * eb, dtype == QW_C64, 0, d.n, c, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(amp_out, tmp, 2 * (size_t)d.n * eb, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaFree(tmp);
+    return e == cudaSuccess ? QW_OK : batch_cuda(b, e, "batch state");
+}
+
+}  // extern "C"

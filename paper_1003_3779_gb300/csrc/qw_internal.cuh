@@ -145,6 +145,8 @@ __device__ __forceinline__ double norm2d(Cx<ff> a) {
 }
 
 // ------------------------------------------------------------------ storage
+// State loads are plain (coherent) global loads, never the read-only path:
+// the batched kernel reads back, in the same launch, what its block wrote.
 // A state buffer is `nslots` plane slots of `pitch` sites each; slot c holds
 // coin c (QW_F32_COMP: slot c the hi parts, slot d+c the lo parts).  pitch is a
 // multiple of 64 sites and the buffer is 256-byte aligned, so every slot is
@@ -170,7 +172,7 @@ template <> struct St<P_F32> {
         reinterpret_cast<float2 *>(v.p)[c * v.pitch + i] = make_float2(a.re, a.im);
     }
     __device__ static void ldv(View v, int c, int64_t i, Cx<float> *o) {
-        float4 a = __ldg(reinterpret_cast<const float4 *>(reinterpret_cast<const float2 *>(v.p) + c * v.pitch + i));
+        float4 a = *reinterpret_cast<const float4 *>(reinterpret_cast<const float2 *>(v.p) + c * v.pitch + i);
         o[0] = {a.x, a.y};
         o[1] = {a.z, a.w};
     }
@@ -186,7 +188,7 @@ template <> struct St<P_F64> {
     static constexpr int SLOT_BYTES = 16;
     static constexpr int SLOTS_PER_COIN = 1;
     __device__ static Cx<double> ld(View v, int c, int64_t i) {
-        double2 a = __ldg(reinterpret_cast<const double2 *>(v.p) + c * v.pitch + i);
+        double2 a = reinterpret_cast<const double2 *>(v.p)[c * v.pitch + i];
         return {a.x, a.y};
     }
     __device__ static void st(View v, int c, int64_t i, Cx<double> a) {
@@ -210,7 +212,7 @@ template <> struct St<P_BF16> {
         reinterpret_cast<__nv_bfloat162 *>(v.p)[c * v.pitch + i] = __floats2bfloat162_rn(a.re, a.im);
     }
     __device__ static void ldv(View v, int c, int64_t i, Cx<float> *o) {
-        uint4 u = __ldg(reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat162 *>(v.p) + c * v.pitch + i));
+        uint4 u = *reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat162 *>(v.p) + c * v.pitch + i);
         const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&u);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -244,8 +246,8 @@ template <> struct St<P_COMP> {
     }
     __device__ static void ldv(View v, int c, int64_t i, Cx<ff> *o) {
         const float2 *p = reinterpret_cast<const float2 *>(v.p);
-        float4 h = __ldg(reinterpret_cast<const float4 *>(p + c * v.pitch + i));
-        float4 l = __ldg(reinterpret_cast<const float4 *>(p + (v.d + c) * v.pitch + i));
+        float4 h = *reinterpret_cast<const float4 *>(p + c * v.pitch + i);
+        float4 l = *reinterpret_cast<const float4 *>(p + (v.d + c) * v.pitch + i);
         o[0] = {{h.x, l.x}, {h.y, l.y}};
         o[1] = {{h.z, l.z}, {h.w, l.w}};
     }

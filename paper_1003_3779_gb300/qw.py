@@ -70,6 +70,9 @@ def lib():
         "qw_batch_probabilities": (I, [P, P, I, P]),
         "qw_batch_get_state": (I, [P, I, P, I]),
         "qw_batch_destroy": (I, [P]),
+        "qw_batch_set_plan": (I, [P, I]),
+        "qw_batch_get_plan": (I, [P, P, P]),
+        "qw_batch_autotune": (I, [P, ctypes.c_char_p, S]),
         "qw_status_string": (ctypes.c_char_p, [I]),
         "qw_last_error": (ctypes.c_char_p, [P]),
         "qw_batch_last_error": (ctypes.c_char_p, [P]),
@@ -338,3 +341,71 @@ class Walk:
 
     def synchronize(self):
         qw_synchronize(self.h)
+
+
+class Batch:
+    """Many independent walks on cycles, advanced in one persistent launch.
+
+    N, T, x0: integer arrays (one entry per walk); coins: (nwalks, 2, 2)
+    complex; coin_state: the two coin amplitudes at x0; prec "f32" or "bf16".
+    """
+
+    def __init__(self, N, T, coins, x0, coin_state=(2 ** -0.5, 1j * 2 ** -0.5), prec="f32",
+                 stream=None):
+        self.N = np.ascontiguousarray(N, dtype=np.int64)
+        self.T = np.ascontiguousarray(T, dtype=np.int64)
+        self.x0 = np.ascontiguousarray(x0, dtype=np.int64)
+        c = np.ascontiguousarray(coins, dtype=np.complex128).reshape(len(self.N), 2, 2)
+        cs = np.ascontiguousarray(coin_state, dtype=np.complex128)
+        self.nwalks = len(self.N)
+        self.offsets = np.concatenate([[0], np.cumsum(self.N)]).astype(np.int64)
+        h = ctypes.c_void_p()
+        st = lib().qw_batch_create(self.nwalks, _ptr(self.N), _ptr(self.T), _ptr(c), _ptr(self.x0),
+                                   _ptr(cs), PRECISIONS[prec] if isinstance(prec, str) else int(prec),
+                                   stream if stream is not None else _stream(), ctypes.byref(h))
+        _check(st)
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qw_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self):
+        _check(lib().qw_batch_step(self.h), self.h, batch=True)
+        return self
+
+    def set_plan(self, k):
+        _check(lib().qw_batch_set_plan(self.h, int(k)), self.h, batch=True)
+        return self
+
+    def plan(self):
+        k, t = ctypes.c_int(), ctypes.c_int()
+        _check(lib().qw_batch_get_plan(self.h, ctypes.byref(k), ctypes.byref(t)), self.h, batch=True)
+        return k.value, t.value
+
+    def autotune(self):
+        buf = ctypes.create_string_buffer(256)
+        _check(lib().qw_batch_autotune(self.h, buf, 256), self.h, batch=True)
+        return buf.value.decode()
+
+    def probabilities(self, out=None):
+        """(P_concat, norms): P of walk i is P_concat[offsets[i]:offsets[i+1]]."""
+        if out is None:
+            out = np.empty(int(self.offsets[-1]), dtype=np.float32)
+        norms = np.empty(self.nwalks, dtype=np.float64)
+        _check(lib().qw_batch_probabilities(self.h, _ptr(out), _on_device(out), _ptr(norms)),
+               self.h, batch=True)
+        return out, norms
+
+    def state(self, walk, dtype=np.complex128):
+        out = np.empty((2, int(self.N[walk])), dtype=dtype)
+        _check(lib().qw_batch_get_state(self.h, int(walk), _ptr(out),
+                                        C64 if dtype == np.complex64 else C128), self.h, batch=True)
+        return out

@@ -1,0 +1,128 @@
+"""Batched walks (one persistent launch replayed from a CUDA graph) against the
+FP64 oracle walk by walk."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1003_3779_gb300 import inputs
+from tests.helpers import amp_tol, maxabs
+
+pytestmark = pytest.mark.gpu
+
+CS = inputs.BATCH_COIN_STATE
+
+
+@pytest.fixture(scope="module")
+def qw():
+    import paper_1003_3779_gb300.qw as qw
+    qw.lib()
+    return qw
+
+
+def oracle_walk(N, T, coin, x0):
+    """Final state of one walk; for 2T+1 < N on the light-cone window only."""
+    if 2 * T + 1 < N:
+        M = 2 * T + 1
+        psi = inputs.localized_1d(M, T, CS)
+        out = oracle.evolve(psi, coin, T)
+        full = np.zeros((2, N), dtype=np.complex128)
+        idx = (x0 - T + np.arange(M)) % N
+        full[:, idx] = out
+        return full
+    return oracle.evolve(inputs.localized_1d(N, x0, CS), coin, T)
+
+
+def small_batch(seed, n):
+    rng = np.random.default_rng(seed)
+    N = rng.integers(1, 3000, size=n)
+    N[:4] = [1, 2, 37, 511]
+    T = rng.integers(0, 700, size=n)
+    T[:3] = [0, 5, 1]
+    x0 = (rng.uniform(size=n) * N).astype(np.int64)
+    coins = np.stack([inputs.su2(th) for th in rng.uniform(0, np.pi / 2, size=n)])
+    return N, T, coins, x0
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+@pytest.mark.parametrize("k", [1, 7, 32, 128])
+def test_batch_matches_oracle_per_walk(qw, prec, k):
+    N, T, coins, x0 = small_batch(1, 24)
+    b = qw.Batch(N, T, coins, x0, CS, prec=prec).set_plan(k)
+    b.step()
+    P, norms = b.probabilities()
+    for i in range(len(N)):
+        want = oracle_walk(int(N[i]), int(T[i]), coins[i], int(x0[i]))
+        got = b.state(i)
+        assert maxabs(got, want) < amp_tol(prec, int(T[i]), k), i
+        Pw = (np.abs(want) ** 2).sum(axis=0)
+        Pi = P[b.offsets[i]:b.offsets[i + 1]]
+        # bfloat16 storage rounds once per round of k steps (no exact pin; loose bound)
+        assert np.abs(Pi - Pw).max() < (1e-6 if prec == "f32" else 5e-2), i
+        assert abs(norms[i] - 1) < (1e-5 if prec == "f32" else 1e-1)
+    b.close()
+
+
+def test_batch_complex_coins_and_repeat(qw):
+    rng = np.random.default_rng(2)
+    N, T, _, x0 = small_batch(3, 16)
+    coins = np.stack([inputs.random_unitary(2, rng) for _ in range(16)])
+    b = qw.Batch(N, T, coins, x0, CS, prec="f32")
+    b.step()
+    P1, n1 = b.probabilities()
+    P1 = P1.copy()
+    b.step()                 # every step restarts from the initial states
+    P2, n2 = b.probabilities()
+    assert np.array_equal(P1, P2) and np.array_equal(n1, n2)
+    for i in range(16):
+        want = oracle_walk(int(N[i]), int(T[i]), coins[i], int(x0[i]))
+        assert maxabs(b.state(i), want) < amp_tol("f32", int(T[i]))
+    b.close()
+
+
+def test_light_cone_zeros_are_exact(qw):
+    N = np.array([60000, 40000, 65536])
+    T = np.array([100, 1000, 2000])
+    x0 = np.array([5, 39990, 30000])
+    coins = np.stack([inputs.su2(0.4)] * 3)
+    b = qw.Batch(N, T, coins, x0, CS)
+    b.step()
+    P, _ = b.probabilities()
+    for i in range(3):
+        Pi = P[b.offsets[i]:b.offsets[i + 1]]
+        dist = np.minimum((np.arange(N[i]) - x0[i]) % N[i], (x0[i] - np.arange(N[i])) % N[i])
+        assert np.all(Pi[dist > T[i]] == 0.0)
+        assert Pi[dist <= T[i]].sum() > 0.999
+    b.close()
+
+
+def test_autotune_batch(qw):
+    N, T, coins, x0 = small_batch(4, 40)
+    b = qw.Batch(N, T, coins, x0, CS)
+    rep = b.autotune()
+    assert '"tuned": true' in rep
+    k, tile = b.plan()
+    assert 8 <= k <= 128 and tile == 16
+    b.step()
+    _, norms = b.probabilities()
+    assert np.abs(norms - 1).max() < 1e-5
+    b.close()
+
+
+@pytest.mark.slow
+def test_full_batch_4096_sampled(qw):
+    """The full batched workload (4096 walks, N~U[256,65536], T~U[64,4096]):
+    every norm is 1, and sampled walks equal the oracle run on their own."""
+    N, T, theta, x0 = inputs.batch_1d_params()
+    coins = np.stack([inputs.su2(th) for th in theta])
+    b = qw.Batch(N, T, coins, x0, CS)
+    b.step()
+    P, norms = b.probabilities()
+    assert np.abs(norms - 1).max() < 1e-4
+    assert np.all(P >= 0)
+    cost = N * np.minimum(T, (2 * T + 1)) + T * np.minimum(N, 2 * T + 1)
+    sample = list(np.argsort(cost)[:4]) + [int(np.argmax(N)), int(np.argmax(T))]
+    for i in sample:
+        want = oracle_walk(int(N[i]), int(T[i]), coins[i], int(x0[i]))
+        Pw = (np.abs(want) ** 2).sum(axis=0)
+        assert np.abs(P[b.offsets[i]:b.offsets[i + 1]] - Pw).sum() < 1e-4, i
+    b.close()
