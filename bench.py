@@ -331,6 +331,57 @@ def run_gpu(args, rank, world, local):
             w2.close()
         del z
 
+    # batched walks: 4096 walks in one persistent launch (graph replay), FP32 and bf16 storage
+    batch = {}
+    if rank == 0 and not args.skip_forms:
+        from paper_1003_3779_gb300 import inputs as _in
+        Nb, Tb, thb, x0b = _in.batch_1d_params()
+        coins_b = np.stack([_in.su2(t) for t in thb])
+        dense = float(np.sum(2.0 * Nb * Tb))
+        tc = np.minimum(Tb, Nb // 2)
+        active = float(np.sum(2.0 * (tc.astype(np.float64) ** 2 + (Tb - tc) * Nb.astype(np.float64))))
+        for pname in ("f32", "bf16"):
+            bt = qw.Batch(Nb, Tb, coins_b, x0b, _in.BATCH_COIN_STATE, prec=pname)
+            tune_b = json.loads(bt.autotune())
+            bt.step()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(3):
+                bt.step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            tb = a.elapsed_time(b) / 1e3 / 3
+            _, nb_ = bt.probabilities()
+            batch[pname] = {"dense_site_coin_updates_per_s": dense / tb,
+                            "active_site_coin_updates_per_s": active / tb, "ms_per_batch": tb * 1e3,
+                            "k": tune_b["k"], "max_norm_err": float(np.abs(nb_ - 1).max())}
+            bt.close()
+
+    # region-mass gradient on the 1024^2 torus (forward with checkpoints + adjoint sweep)
+    grad_leg = {}
+    if rank == 0 and not args.skip_forms:
+        from paper_1003_3779_gb300 import inputs as _in
+        Lg, Tg, Kg = 1024, 512, 64
+        wg = qw.Walk((Lg, Lg), prec="f32")
+        phi_g = torch.from_numpy(_in.region_grad_phases(Lg).reshape(-1, 4).astype(np.float32)).cuda()
+        wg.set_coin_phases(_in.grover(), phi_g)
+        psi_g = torch.from_numpy(_in.localized_2d(Lg).astype(np.complex64)).cuda()
+        g_out = torch.empty((Lg * Lg, 4), dtype=torch.float64, device=f"cuda:{local}")
+        wg.set_state(psi_g)
+        qw.qw_backward(wg.h, _in.region_rect(Lg), Tg, Kg, g_out)
+        torch.cuda.synchronize()
+        t0g = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            wg.set_state(psi_g)
+            lossg = qw.qw_backward(wg.h, _in.region_rect(Lg), Tg, Kg, g_out)
+        torch.cuda.synchronize()
+        tg = (time.perf_counter() - t0g) / reps
+        grad_leg = {"ms": tg * 1e3, "loss": lossg,
+                    "site_steps_per_s": 2.0 * Tg * Lg * Lg / tg,
+                    "note": "forward T steps with checkpoints + T adjoint steps, host wall clock"}
+        wg.close()
+
     # accuracy and the other precision forms on the same input (rank 0 only)
     forms, accuracy = {}, {}
     if rank == 0 and not args.skip_forms:
@@ -398,7 +449,7 @@ def run_gpu(args, rank, world, local):
         "value": value, "elapsed": tmax, "norm": norm, "roofline": roof, "roofline_k1": roof_k1,
         "forms": forms, "accuracy": accuracy, "e2e": e2e, "clocks": clk.summary(), "tune": tune,
         "K": K, "tile": tile, "launches": args.steps * (launches_step + 2), "dist": dist,
-        "torus": torus,
+        "torus": torus, "batch": batch, "grad": grad_leg,
     }
 
 
@@ -454,6 +505,7 @@ def main():
         "clocks": r["clocks"], "e2e": r["e2e"], "gpu_launches": r["launches"],
         "roofline": r["roofline"], "roofline_k1": r["roofline_k1"], "cpu_baseline": cpu,
         "accuracy": r["accuracy"], "forms": r["forms"], "torus_8192_k1": r["torus"],
+        "batch_4096": r["batch"], "region_grad_1024": r["grad"],
         "norm": r["norm"], "autotune": r["tune"],
     }
     print(json.dumps(out))

@@ -409,3 +409,35 @@ class Batch:
         _check(lib().qw_batch_get_state(self.h, int(walk), _ptr(out),
                                         C64 if dtype == np.complex64 else C128), self.h, batch=True)
         return out
+
+
+def _region_mass_function():
+    import torch
+
+    class RegionMass(torch.autograd.Function):
+        """loss = probability mass in rect after T steps on the torus, as a
+        function of the per-site coin phases phi (nsites x 4, float32, CUDA);
+        C_v = base . diag(e^{i phi_v}).  Forward and backward both come from one
+        qw_backward call (forward pass with checkpoints every K steps, then the
+        U^dagger sweep); backward returns grad_output * dL/dphi."""
+
+        @staticmethod
+        def forward(ctx, phi, walk, base, psi0, rect, T, K):
+            qw_set_coin_phases(walk.h, base, phi)
+            qw_set_state(walk.h, psi0)
+            grad = torch.empty((walk.nsites, 4), dtype=torch.float64, device=phi.device)
+            loss = qw_backward(walk.h, rect, T, K, grad)
+            ctx.save_for_backward(grad)
+            return torch.tensor(loss, dtype=torch.float64, device=phi.device)
+
+        @staticmethod
+        def backward(ctx, grad_output):
+            (grad,) = ctx.saved_tensors
+            return (grad_output * grad).to(torch.float32), None, None, None, None, None, None
+
+    return RegionMass
+
+
+def region_mass(phi, walk, base, psi0, rect, T, K=64):
+    """Differentiable region mass (see RegionMass)."""
+    return _region_mass_function().apply(phi, walk, base, psi0, rect, T, K)
