@@ -179,15 +179,15 @@ def cpu_oracle_sample(target_s=12.0):
 # ------------------------------------------------------------------ GPU arm
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("k_step1d.cuh", "qw_internal.cuh", "launch_step.cuh"):
+    for f in ("k_step1d.cuh", "qw_internal.cuh", "launch_step.cuh"):  # every 1D step kernel lives here
         h.update(open(os.path.join(ROOT, "paper_1003_3779_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic():
+def ncu_traffic(kernel="k_step1d_sweep"):
     """DRAM bytes per launch of the 1D step kernel from the committed ncu summary,
     or None when the summary is missing or was taken on different kernel sources."""
-    p = os.path.join(ROOT, "profiles", "k_step1d_su2_f32.md")
+    p = os.path.join(ROOT, "profiles", f"{kernel}_su2_f32.md")
     try:
         s = open(p).read()
     except OSError:
@@ -220,8 +220,8 @@ def run_gpu(args, rank, world, local):
     w.set_coin(C)
     w.set_state(dev0)
     if args.plan:
-        pk, pt = (int(x) for x in args.plan.split(","))
-        w.set_plan(pk, pt)
+        f = [int(x) for x in args.plan.split(",")]
+        w.set_plan_ex(f[0], f[1], f[2] if len(f) > 2 else 1)
         tune = {"tuned": False, "plan": args.plan}
     else:
         tune = json.loads(w.autotune())
@@ -275,7 +275,7 @@ def run_gpu(args, rank, world, local):
     ach_tflops = flops_launch / avg_launch_s / 1e12
     ach_gbs = bytes_launch / avg_launch_s / 1e9
     alu_frac, hbm_frac = ach_tflops / alu_peak, ach_gbs / hbm_gbs
-    traffic = ncu_traffic()
+    traffic = ncu_traffic(desc["path"])
     if alu_frac >= hbm_frac:
         roof = {"bound": "alu", "achieved": ach_tflops, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": alu_frac, "traffic": traffic,
@@ -287,12 +287,14 @@ def run_gpu(args, rank, world, local):
         roof = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm_gbs, "unit": "GB/s",
                 "frac": hbm_frac, "traffic": traffic, "peak_source": f"{peak_src} HBM copy",
                 "alu_view": {"achieved_tflops": ach_tflops, "peak_tflops": alu_peak, "frac": alu_frac}}
-    roof.update({"kernel": "k_step1d<f32,R=%d,%s coin>" % (tile, desc["coin_kind"]), "k": K,
+    roof.update({"kernel": "%s<f32,R=%d,%s coin>" % (desc["path"], 16 if desc["path"] == "k_step1d_sweep" else tile,
+                                                     desc["coin_kind"]), "k": K,
                  "flops_per_site_step": flops_site_step,
                  "avg_launch_ms": avg_launch_s * 1e3,
                  "effective_bytes_per_site_step": bytes_launch / N_SITES / k_eff})
 
     # k = 1 (one step per HBM round trip): the plain fused step against the HBM roof
+    plan_saved = w.plan_ex()
     w.set_plan(1, tile)
     qw.qw_set_state(w.h, dev0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -305,7 +307,7 @@ def run_gpu(args, rank, world, local):
     roof_k1 = {"bound": "hbm", "achieved": 32.0 * N_SITES / k1_s / 1e9, "peak": hbm_gbs,
                "unit": "GB/s", "frac": 32.0 * N_SITES / k1_s / 1e9 / hbm_gbs,
                "frac_of_8000": 32.0 * N_SITES / k1_s / 1e9 / 8000.0}
-    w.set_plan(K, tile)
+    w.set_plan_ex(*plan_saved)
 
     # the torus: the fused 2D step (k = 1) on the 8192^2 lattice, against the HBM roof
     torus = {}
@@ -464,7 +466,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--n-sites", type=int, default=N_SITES,
                     help="cycle length (default 2^27; smaller only for profiling captures)")
-    ap.add_argument("--plan", default="", help="fixed 'k,tile' instead of the autotuner")
+    ap.add_argument("--plan", default="",
+                    help="fixed 'k,tile[,variant]' instead of the autotuner (variant 1 = sweep, the default; 0 = tiles)")
     args = ap.parse_args()
     rank, world, local = dist_env()
 

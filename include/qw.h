@@ -144,6 +144,16 @@ qw_status qw_probabilities(qw_walk *w, void *P_out, qw_rdtype pdtype, int on_dev
 qw_status qw_set_plan(qw_walk *w, int depth_k, int tile);
 qw_status qw_get_plan(const qw_walk *w, int *depth_k, int *tile);
 
+/* The same with the 1D kernel variant: 0 = independent warp tiles (each warp
+ * recomputes a halo of k sites on both sides), 1 = time-skewed sweep (a warp
+ * walks a segment chunk by chunk in a frame that slides one site per step and
+ * hands two values per step to the next chunk; no halo except one warm-up
+ * chunk per segment).  Variant 1 needs the periodic cycle, N a multiple of its
+ * chunk (512 sites; 256 in FP64), a global coin, FP32 / BF16 / FP64 and
+ * k < chunk / 2, else QW_EINVAL.  qw_set_plan selects variant 0. */
+qw_status qw_set_plan_ex(qw_walk *w, int depth_k, int tile, int variant);
+qw_status qw_get_plan_ex(const qw_walk *w, int *depth_k, int *tile, int *variant);
+
 /* Time the candidate plans on this walk (CUDA events on the walk's stream,
  * reading the current state, writing only the scratch buffer, so the state is
  * unchanged) and keep the fastest.  Results are cached per (lattice shape,

@@ -343,4 +343,179 @@ k_step1d_k1(View in, View out, int64_t n, int64_t nwarps, CoinP<typename St<P>::
     S::stv(out, 1, xs, r1);
 }
 
+// ---------------------------------------------------------------- time-skewed sweep
+// The same k steps per HBM round trip as tb_tile, without recomputing a halo.
+// A warp walks a segment of the cycle chunk by chunk (32R sites per chunk).
+// The frame slides one site to the left per step: after t steps a chunk that
+// was loaded at [x, x + 32R) holds [x - t, x + 32R - t).  In that frame the
+// walk depends on the left only: one plane keeps its index, the other takes
+// the value two sites to its left (moving shift: coin 0 arrives from x+1, coin
+// 1 from x-1).  The two values a chunk needs from the chunk before it, at each
+// of the k time levels, are handed over through a small per-warp edge array in
+// shared memory.  Only the first chunk of a segment is recomputed (a warm-up
+// chunk whose own left edge starts as zeros; its error front moves two sites
+// per step, so k < 16R keeps the handed-over values exact).  The next chunk is
+// prefetched with cp.async into a swizzled shared buffer while the current one
+// computes; each lane then reads its own run conflict-free.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Position of a lane's c-th 16-byte unit in the chunk buffer: the XOR keeps the
+// eight lanes that share a shared-memory wavefront on distinct bank groups.
+template <int CPL>
+__device__ __forceinline__ int swz(int lane, int c) {
+    constexpr int G = 8 / CPL;
+    return lane * CPL + (c ^ ((lane / G) & (CPL - 1)));
+}
+
+template <int P, int R>
+struct Sweep {
+    static constexpr int B = 32 * R;                              // sites per chunk
+    static constexpr int CPL = R * St<P>::SLOT_BYTES / 16;        // 16-byte units per lane and plane
+    static constexpr size_t chunk_bytes = 2 * 32 * CPL * 16;
+    __host__ __device__ static size_t edge_bytes(int K) { return 2 * (size_t)K * 2 * sizeof(Cx<typename St<P>::real>); }
+    __host__ __device__ static size_t warp_bytes(int K) { return chunk_bytes + edge_bytes(K); }
+};
+
+template <int P, int R, int CK, int FF, int ADJ>
+__global__ void __launch_bounds__(128)
+k_step1d_sweep(View in, View out, int64_t n, int K, int nch, int64_t nseg, CoinP<typename St<P>::real> cp,
+               typename St<P>::real pre0, typename St<P>::real pre1,
+               typename St<P>::real post0, typename St<P>::real post1) {
+    using S = St<P>;
+    using real = typename S::real;
+    using C = Cx<real>;
+    using SW = Sweep<P, R>;
+    constexpr int B = SW::B, CPL = SW::CPL, VEC = S::VEC;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t seg = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (seg >= nseg) return;   // uniform per warp
+    unsigned char *wbase = smem + wib * SW::warp_bytes(K);
+    uint4 *cbuf = reinterpret_cast<uint4 *>(wbase);
+    C *edge = reinterpret_cast<C *>(wbase + SW::chunk_bytes);
+    const int64_t s0 = seg * (int64_t)nch * B;
+    const int nchs = (int)min((int64_t)nch, (n - s0) / B);
+
+    auto prefetch = [&](int j) {
+        int64_t start = s0 + (int64_t)j * B;
+        if (start < 0) start += n;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const char *g = static_cast<const char *>(in.p) + (c * in.pitch + start) * S::SLOT_BYTES;
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                const int u = i * 32 + lane;
+                cp_async16(cbuf + c * 32 * CPL + swz<CPL>(u / CPL, u % CPL), g + (size_t)u * 16);
+            }
+        }
+        cp_async_commit();
+    };
+
+    C a0[R], a1[R];
+    prefetch(-1);
+    for (int j = -1; j < nchs; ++j) {
+        cp_async_wait_all();
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < CPL; ++u) {
+            S::unpack(cbuf[swz<CPL>(lane, u)], &a0[u * VEC]);
+            S::unpack(cbuf[32 * CPL + swz<CPL>(lane, u)], &a1[u * VEC]);
+        }
+        __syncwarp();
+        if (j + 1 < nchs) prefetch(j + 1);
+        if (!is_one(pre0)) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) a0[i] = rmul(pre0, a0[i]);
+        }
+        if (!is_one(pre1)) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) a1[i] = rmul(pre1, a1[i]);
+        }
+        const int par = j & 1;
+        const C *ein = edge + (size_t)(par ^ 1) * K * 2;   // handed over by the previous chunk
+        C *eout = edge + (size_t)par * K * 2;
+        // One level of the sliding frame, from (s0, s1) into fresh arrays (d0, d1).
+        // Two levels per loop iteration ping-pong between a and b, so results
+        // always go to registers that hold nothing live (no moves at all).
+        auto level = [&](int t, const C (&s0)[R], const C (&s1)[R], C (&d0)[R], C (&d1)[R]) {
+            const C h2 = j >= 0 ? ein[2 * t] : czero<real>(), h1 = j >= 0 ? ein[2 * t + 1] : czero<real>();
+            if (!ADJ) {
+                C top2, top1;   // coin-1 results of the two highest sites: they leave the lane
+#pragma unroll
+                for (int i = R - 1; i >= 0; --i) {
+                    C n0, n1;
+                    coin2<CK>(cp, (const C *)nullptr, s0[i], s1[i], n0, n1);
+                    // moving: coin 0 keeps its frame index, coin 1 moves two up;
+                    // flip-flop: the same values land in the other plane
+                    if (!FF) d0[i] = n0; else d1[i] = n0;
+                    if (i + 2 < R) { if (!FF) d1[i + 2] = n1; else d0[i + 2] = n1; }
+                    else if (i == R - 1) top1 = n1;
+                    else top2 = n1;
+                }
+                C lm2 = shfl_up(top2, 1), lm1 = shfl_up(top1, 1);
+                // edge hand-over without divergence: every lane reads the broadcast
+                // value, lane 0 selects it; lane 31's store is a predicated store
+                lm2 = lane == 0 ? h2 : lm2;
+                lm1 = lane == 0 ? h1 : lm1;
+                if (lane == 31) { eout[2 * t] = top2; eout[2 * t + 1] = top1; }
+                if (!FF) { d1[0] = lm2; d1[1] = lm1; } else { d0[0] = lm2; d0[1] = lm1; }
+            } else {
+                // S^dagger in the sliding frame: moving b1 = a1 (same index), b0 = a0 two down;
+                // flip-flop b1 = a0, b0 = a1 two down.  Then C^dagger at the site.
+                const C e2 = FF ? s1[R - 2] : s0[R - 2], e1 = FF ? s1[R - 1] : s0[R - 1];
+                C lm2 = shfl_up(e2, 1), lm1 = shfl_up(e1, 1);
+                lm2 = lane == 0 ? h2 : lm2;
+                lm1 = lane == 0 ? h1 : lm1;
+                if (lane == 31) { eout[2 * t] = e2; eout[2 * t + 1] = e1; }
+#pragma unroll
+                for (int i = R - 1; i >= 0; --i) {
+                    const C b0 = i >= 2 ? (FF ? s1[i - 2] : s0[i - 2]) : (i == 0 ? lm2 : lm1);
+                    const C b1 = FF ? s0[i] : s1[i];
+                    coin2_adj<CK>(cp, (const C *)nullptr, b0, b1, d0[i], d1[i]);
+                }
+            }
+        };
+        C b0[R], b1[R];
+        int t = 0;
+#pragma unroll 1
+        for (; t + 1 < K; t += 2) {
+            level(t, a0, a1, b0, b1);
+            level(t + 1, b0, b1, a0, a1);
+        }
+        if (t < K) {
+            level(t, a0, a1, b0, b1);
+#pragma unroll
+            for (int i = 0; i < R; ++i) { a0[i] = b0[i]; a1[i] = b1[i]; }
+        }
+        __syncwarp();   // this chunk's edges are visible to lane 0 of the next one
+        if (j >= 0) {
+            if (!is_one(post0)) {
+#pragma unroll
+                for (int i = 0; i < R; ++i) a0[i] = rmul(post0, a0[i]);
+            }
+            if (!is_one(post1)) {
+#pragma unroll
+                for (int i = 0; i < R; ++i) a1[i] = rmul(post1, a1[i]);
+            }
+            const int64_t g0 = s0 + (int64_t)j * B - K + lane * R;
+            if (g0 >= 0 && g0 + R <= n && (g0 % VEC) == 0) {
+#pragma unroll
+                for (int i = 0; i < R; i += VEC) { S::stv(out, 0, g0 + i, &a0[i]); S::stv(out, 1, g0 + i, &a1[i]); }
+            } else {
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const int64_t g = wrap_index(g0 + i, n);
+                    S::st(out, 0, g, a0[i]);
+                    S::st(out, 1, g, a1[i]);
+                }
+            }
+        }
+    }
+}
+
 }  // namespace qw

@@ -7,6 +7,8 @@
 #include "k_step2d.cuh"
 #include "k_generic.cuh"
 
+#include <algorithm>
+
 namespace qw {
 
 // Sites per lane compiled for the 1D kernel: two forward tiles, and the
@@ -77,6 +79,62 @@ static bool go1d_kind(const Step1DArgs &a, const CoinP<typename St<P>::real> &cp
     }
 }
 
+// Sites per lane of the sweep kernel (one 16-byte unit count per lane that is a
+// power of two between 2 and 8); the double-float form has no sweep kernel.
+template <int P> struct SweepR { static constexpr int R = 16; };
+template <> struct SweepR<P_F64> { static constexpr int R = 8; };
+
+template <int P, int CK, int FF, int ADJ>
+static cudaError_t go1d_sweep(const Step1DArgs &a, const CoinP<typename St<P>::real> &cp, cudaStream_t s) {
+    using real = typename St<P>::real;
+    constexpr int R = SweepR<P>::R;
+    using SW = Sweep<P, R>;
+    constexpr int warps = 4;
+    const size_t smem = warps * SW::warp_bytes(a.K);
+    auto kfn = k_step1d_sweep<P, R, CK, FF, ADJ>;
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // Segments sized so that the whole launch is one wave of resident warps:
+    // every warp sweeps about the same number of chunks, and the one warm-up
+    // chunk per segment is a small fraction of it.
+    int nch = a.chunks;
+    if (nch <= 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * warps, smem);
+        const int64_t resident = (int64_t)std::max(1, sms) * std::max(1, per_sm) * warps;
+        const int64_t chunks = a.n / SW::B;
+        nch = (int)std::max<int64_t>(1, (chunks + resident - 1) / resident);
+    }
+    const int64_t nseg = (a.n / SW::B + nch - 1) / nch;
+    const int64_t blocks = (nseg + warps - 1) / warps;
+    kfn<<<(unsigned)blocks, 32 * warps, smem, s>>>(a.in, a.out, a.n, a.K, nch, nseg, cp,
+                                                  real_from_double<real>(a.pre0), real_from_double<real>(a.pre1),
+                                                  real_from_double<real>(a.post0), real_from_double<real>(a.post1));
+    return cudaGetLastError();
+}
+
+template <int P, int ADJ>
+static cudaError_t go1d_sweep_kind(const Step1DArgs &a, const CoinP<typename St<P>::real> &cp, cudaStream_t s) {
+    const bool ff = a.shift == QW_SHIFT_FLIPFLOP;
+    switch (a.kind) {
+        case CK_REAL: return ff ? go1d_sweep<P, CK_REAL, 1, ADJ>(a, cp, s) : go1d_sweep<P, CK_REAL, 0, ADJ>(a, cp, s);
+        case CK_COMPLEX: return ff ? go1d_sweep<P, CK_COMPLEX, 1, ADJ>(a, cp, s) : go1d_sweep<P, CK_COMPLEX, 0, ADJ>(a, cp, s);
+        case CK_SIGN_P: return ff ? cudaErrorInvalidValue : go1d_sweep<P, CK_SIGN_P, 0, ADJ>(a, cp, s);
+        case CK_SIGN_M: return ff ? cudaErrorInvalidValue : go1d_sweep<P, CK_SIGN_M, 0, ADJ>(a, cp, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Can the sweep kernel run this launch?  (n a multiple of the chunk, 2 <= K < chunk / 2.)
+template <int P>
+bool sweep_ok(int64_t n, int K, int kind) {
+    if (P == P_COMP || kind == CK_PERSITE || kind == CK_PHASE) return false;
+    constexpr int B = Sweep<P, SweepR<P>::R>::B;
+    return n % B == 0 && n >= B && K >= 2 && K <= B / 2 - 1;
+}
+
 // Largest K the 1D kernel accepts for tile R: at least half the tile is output.
 inline int max_k_1d(int R) { return 8 * R; }
 
@@ -93,6 +151,14 @@ cudaError_t step1d_t(const Step1DArgs &a0, const void *coinp, int adj, cudaStrea
     const auto &cp = *static_cast<const CoinP<typename St<P>::real> *>(coinp);
     Step1DArgs a = a0;
     a.tile = tile1d_effective<P>(a.tile, a.kind, adj);
+    if (a.variant == 1) {   // time-skewed sweep
+        if constexpr (P == P_COMP) {
+            return cudaErrorInvalidValue;
+        } else {
+            if (!sweep_ok<P>(a.n, a.K, a.kind)) return cudaErrorInvalidValue;
+            return adj ? go1d_sweep_kind<P, 1>(a, cp, s) : go1d_sweep_kind<P, 0>(a, cp, s);
+        }
+    }
     if (a.K < 1 || a.K > max_k_1d(a.tile)) return cudaErrorInvalidValue;
     const bool ff = a.shift == QW_SHIFT_FLIPFLOP;
     if (a.K == 1) {   // one step per launch: the streaming kernel
@@ -191,4 +257,5 @@ cudaError_t generic_t(const StepGenericArgs &a, const void *coinp, cudaStream_t 
         return generic_t<PREC>(a, cp, s);                                                               \
     }                                                                                                   \
     int tile1d_##SUFFIX(int tile, int kind, int adj) { return tile1d_effective<PREC>(tile, kind, adj); } \
+    bool sweep_ok_##SUFFIX(int64_t n, int K, int kind) { return sweep_ok<PREC>(n, K, kind); }          \
     }

@@ -93,24 +93,48 @@ static int tile1d(int prec, int tile, int kind, int adj) {
     }
     return 0;
 }
+static bool sweep_ok(const qw_walk *w, int K) {
+    if (w->ndim != 1 || w->bc != QW_BC_PERIODIC || w->has_links) return false;
+    switch (w->prec) {
+        case QW_F64: return sweep_ok_f64(w->nx, K, w->kind);
+        case QW_F32: return sweep_ok_f32(w->nx, K, w->kind);
+        case QW_F32_BF16STORE: return sweep_ok_bf16(w->nx, K, w->kind);
+    }
+    return false;
+}
+static int sweep_max_k(const qw_walk *w) { return w->prec == QW_F64 ? 127 : 255; }
+
 // tiles compiled for the forward 1D kernel, per precision
 static void tiles_of(int prec, int &a, int &b) {
     if (prec == QW_F64 || prec == QW_F32_COMP) { a = 4; b = 8; }
     else { a = 8; b = 16; }
 }
 
-static void default_plan(const qw_walk *w, int &k, int &tile) {
+static void default_plan(const qw_walk *w, int &k, int &tile, int &variant) {
+    variant = 0;
     if (w->ndim == 2) { k = 1; tile = 0; return; }
     switch (w->prec) {
         case QW_F64: tile = 8; k = 8; break;
         case QW_F32_COMP: tile = 4; k = 8; break;
         default: tile = 16; k = 32; break;
     }
+    if (sweep_ok(w, w->prec == QW_F64 ? 8 : 64)) {
+        variant = 1;
+        k = w->prec == QW_F64 ? 8 : 64;
+    }
 }
 
+static void effective_plan(const qw_walk *w, int &k, int &tile, int &variant) {
+    default_plan(w, k, tile, variant);
+    if (w->plan_k > 0) {
+        k = w->plan_k;
+        tile = w->plan_tile ? w->plan_tile : tile;
+        variant = w->plan_variant >= 0 ? w->plan_variant : 0;
+    }
+}
 static void effective_plan(const qw_walk *w, int &k, int &tile) {
-    default_plan(w, k, tile);
-    if (w->plan_k > 0) { k = w->plan_k; tile = w->plan_tile ? w->plan_tile : tile; }
+    int v;
+    effective_plan(w, k, tile, v);
 }
 
 // Global coin: store, classify, and convert to the compute precision.
@@ -260,14 +284,17 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
         return QW_OK;
     }
     if (w->ndim == 1) {
-        int K, tile;
-        effective_plan(w, K, tile);
+        int K, tile, variant;
+        effective_plan(w, K, tile, variant);
         const int teff = tile1d(w->prec, tile, w->kind, adj);
-        K = std::min(K, 8 * teff);
+        if (variant != 1) K = std::min(K, 8 * teff);
         Step1DArgs a{};
         a.n = w->nx; a.tile = teff; a.shift = w->shift; a.kind = w->kind; a.coins = w->coins_dev;
         for (int64_t rem = T; rem > 0;) {
             a.K = (int)std::min<int64_t>(K, rem);
+            // the last, shorter launch of a sweep plan falls back to the tile kernel if needed
+            a.variant = (variant == 1 && sweep_ok(w, a.K)) ? 1 : 0;
+            if (a.variant == 0) a.K = std::min(a.K, 8 * teff);
             launch_gains_1d(w, a.K, adj, a);
             a.in = cur_view(w); a.out = next_view(w);
             if ((e = step1d(w->prec, a, cp, adj, w->stream)) != cudaSuccess) return cuda_error(w, e, "1D step launch");
@@ -607,12 +634,38 @@ qw_status qw_set_plan(qw_walk *w, int depth_k, int tile) {
         w->plan_k = 1; w->plan_tile = 0; w->plan_user = true;
         return QW_OK;
     }
-    int dk, dt;
-    default_plan(w, dk, dt);
+    int dk, dt, dv;
+    default_plan(w, dk, dt, dv);
     const int teff = tile1d(w->prec, tile ? tile : dt, CK_REAL, 0);
     if (tile && teff != tile) return set_error(w, QW_EINVAL, "tile not compiled for this precision");
     if (depth_k > 8 * teff) return set_error(w, QW_EINVAL, "k exceeds 8 * tile");
-    w->plan_k = depth_k; w->plan_tile = teff; w->plan_user = true;
+    w->plan_k = depth_k; w->plan_tile = teff; w->plan_variant = 0; w->plan_user = true;
+    return QW_OK;
+}
+
+qw_status qw_set_plan_ex(qw_walk *w, int depth_k, int tile, int variant) {
+    if (!w) return QW_EINVAL;
+    if (variant != 1) {
+        qw_status st = qw_set_plan(w, depth_k, tile);
+        if (st == QW_OK && depth_k == 0) w->plan_variant = -1;
+        return st;
+    }
+    if (w->ndim != 1 || depth_k < 1 || depth_k > sweep_max_k(w) || !sweep_ok(w, std::max(depth_k, 2)))
+        return set_error(w, QW_EINVAL, "the sweep kernel needs the periodic 1D walk, N a multiple of its "
+                                       "chunk, a global coin, FP32/BF16/FP64 and 1 <= k < chunk / 2");
+    int dk, dt, dv;
+    default_plan(w, dk, dt, dv);
+    w->plan_k = depth_k; w->plan_tile = tile1d(w->prec, tile ? tile : dt, CK_REAL, 0); w->plan_variant = 1;
+    w->plan_user = true;
+    return QW_OK;
+}
+
+qw_status qw_get_plan_ex(const qw_walk *w, int *depth_k, int *tile, int *variant) {
+    if (!w || !depth_k || !tile || !variant) return QW_EINVAL;
+    int k, t, v;
+    effective_plan(w, k, t, v);
+    if (w->ndim == 1) t = tile1d(w->prec, t, w->kind, 0);
+    *depth_k = k; *tile = t; *variant = v;
     return QW_OK;
 }
 
@@ -620,8 +673,8 @@ qw_status qw_describe(const qw_walk *w, char *buf, size_t len) {
     if (!w || !buf || !len) return QW_EINVAL;
     static const char *kinds[] = {"real", "complex", "grover", "hadamard2", "per_site", "phase",
                                   "hadamard_class", "hadamard_class"};
-    int k, t;
-    effective_plan(w, k, t);
+    int k, t, var;
+    effective_plan(w, k, t, var);
     if (w->ndim == 1) t = tile1d(w->prec, t, w->kind, 0);
     const bool generic = w->bc != QW_BC_PERIODIC || w->has_links ||
                          (w->ndim == 2 && (w->kind == CK_PERSITE ||
@@ -630,7 +683,8 @@ qw_status qw_describe(const qw_walk *w, char *buf, size_t len) {
                   "{\"ndim\": %d, \"sites\": %lld, \"coin_dim\": %d, \"precision\": %d, \"coin_kind\": \"%s\", "
                   "\"k\": %d, \"tile\": %d, \"path\": \"%s\", \"state_bytes\": %zu}",
                   w->ndim, (long long)w->ns, w->d, w->prec, kinds[w->kind], k, t,
-                  generic ? "generic" : (w->ndim == 1 ? "k_step1d" : "k_step2d"), w->state_bytes);
+                  generic ? "generic" : (w->ndim == 1 ? (var == 1 ? "k_step1d_sweep" : "k_step1d") : "k_step2d"),
+                  w->state_bytes);
     return QW_OK;
 }
 
@@ -709,7 +763,8 @@ extern "C" qw_status qw_autotune(qw_walk *w, char *report, size_t report_len) {
     auto it = g_tune.find(key);
     char buf[512];
     if (it != g_tune.end()) {
-        w->plan_tile = it->second.first;
+        w->plan_tile = std::abs(it->second.first);   // a negative tile records the sweep kernel
+        w->plan_variant = it->second.first < 0 ? 1 : 0;
         w->plan_k = it->second.second;
         std::snprintf(buf, sizeof buf, "{\"tuned\": true, \"cached\": true, \"key\": \"%s\", \"tile\": %d, \"k\": %d}",
                       key.c_str(), w->plan_tile, w->plan_k);
@@ -750,16 +805,39 @@ extern "C" qw_status qw_autotune(qw_walk *w, char *report, size_t report_len) {
         }
         if (err != cudaSuccess) break;
     }
+    int best_v = 0;
+    if (err == cudaSuccess) {
+        const int sks[] = {8, 16, 24, 32, 48, 64, 96, 128, 160, 192, 255};
+        for (int k : sks) {
+            if (k > sweep_max_k(w) || !sweep_ok(w, k)) continue;
+            a.K = k; a.variant = 1;
+            launch_gains_1d(w, k, 0, a, false);
+            err = step1d(w->prec, a, w->coinp, 0, w->stream);
+            if (err != cudaSuccess) break;
+            cudaEventRecord(e0, w->stream);
+            const int reps = 3;
+            for (int r = 0; r < reps; ++r) step1d(w->prec, a, w->coinp, 0, w->stream);
+            cudaEventRecord(e1, w->stream);
+            if ((err = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const float per_step = ms / (reps * k);
+            if (per_step < best) { best = per_step; best_k = k; best_v = 1; }
+        }
+        a.variant = 0;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (err != cudaSuccess) return cuda_error(w, err, "autotune");
     w->plan_tile = best_t;
     w->plan_k = best_k;
-    g_tune[key] = {best_t, best_k};
+    w->plan_variant = best_v;
+    g_tune[key] = {best_v ? -best_t : best_t, best_k};
     tune_save();
     std::snprintf(buf, sizeof buf,
-                  "{\"tuned\": true, \"cached\": false, \"key\": \"%s\", \"tile\": %d, \"k\": %d, \"ms_per_step\": %.6g}",
-                  key.c_str(), best_t, best_k, best);
+                  "{\"tuned\": true, \"cached\": false, \"key\": \"%s\", \"tile\": %d, \"k\": %d, "
+                  "\"variant\": \"%s\", \"ms_per_step\": %.6g}",
+                  key.c_str(), best_t, best_k, best_v ? "sweep" : "tiles", best);
     put(buf);
     return QW_OK;
 }

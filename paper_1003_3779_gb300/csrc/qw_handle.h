@@ -49,6 +49,7 @@ struct qw_walk {
 
     // execution plan
     int plan_k = 0, plan_tile = 0;
+    int plan_variant = -1;   // 1D kernel: -1 automatic, 0 independent warp tiles, 1 time-skewed sweep
     bool plan_user = false;
 
     // adjoint / gradient scratch
@@ -88,6 +89,9 @@ cudaError_t launch_generic_f32(const StepGenericArgs &, const void *, cudaStream
 cudaError_t launch_generic_f64(const StepGenericArgs &, const void *, cudaStream_t);
 cudaError_t launch_generic_bf16(const StepGenericArgs &, const void *, cudaStream_t);
 cudaError_t launch_generic_comp(const StepGenericArgs &, const void *, cudaStream_t);
+bool sweep_ok_f32(int64_t, int, int);
+bool sweep_ok_f64(int64_t, int, int);
+bool sweep_ok_bf16(int64_t, int, int);
 int tile1d_f32(int, int, int);
 int tile1d_f64(int, int, int);
 int tile1d_bf16(int, int, int);

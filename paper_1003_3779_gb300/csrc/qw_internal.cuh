@@ -180,6 +180,10 @@ template <> struct St<P_F32> {
         *reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(v.p) + c * v.pitch + i) =
             make_float4(a[0].re, a[0].im, a[1].re, a[1].im);
     }
+    __device__ static void unpack(uint4 u, Cx<float> *o) {
+        o[0] = {__uint_as_float(u.x), __uint_as_float(u.y)};
+        o[1] = {__uint_as_float(u.z), __uint_as_float(u.w)};
+    }
 };
 
 template <> struct St<P_F64> {
@@ -196,6 +200,9 @@ template <> struct St<P_F64> {
     }
     __device__ static void ldv(View v, int c, int64_t i, Cx<double> *o) { o[0] = ld(v, c, i); }
     __device__ static void stv(View v, int c, int64_t i, const Cx<double> *a) { st(v, c, i, a[0]); }
+    __device__ static void unpack(uint4 u, Cx<double> *o) {
+        o[0] = {__hiloint2double(u.y, u.x), __hiloint2double(u.w, u.z)};
+    }
 };
 
 template <> struct St<P_BF16> {
@@ -226,6 +233,14 @@ template <> struct St<P_BF16> {
 #pragma unroll
         for (int k = 0; k < 4; ++k) b[k] = __floats2bfloat162_rn(a[k].re, a[k].im);
         *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat162 *>(v.p) + c * v.pitch + i) = u;
+    }
+    __device__ static void unpack(uint4 u, Cx<float> *o) {
+        const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float2 f = __bfloat1622float2(b[k]);
+            o[k] = {f.x, f.y};
+        }
     }
 };
 
@@ -312,6 +327,8 @@ struct Step1DArgs {
     const void *coins; // CK_PERSITE: nsites x 4 complex in compute precision
     double pre0, pre1;   // per-plane factors applied after the load
     double post0, post1; // per-plane factors applied before the store
+    int variant;         // 0 independent warp tiles (halo recomputed), 1 time-skewed sweep
+    int chunks;          // sweep: chunks per warp segment (0 = default)
 };
 cudaError_t launch_step1d(int prec, const Step1DArgs &a, const void *coinp, cudaStream_t s);
 cudaError_t launch_step1d_adjoint(int prec, const Step1DArgs &a, const void *coinp, cudaStream_t s);

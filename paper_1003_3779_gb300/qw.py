@@ -60,6 +60,8 @@ def lib():
         "qw_probabilities": (I, [P, P, I, I, P]),
         "qw_set_plan": (I, [P, I, I]),
         "qw_get_plan": (I, [P, P, P]),
+        "qw_set_plan_ex": (I, [P, I, I, I]),
+        "qw_get_plan_ex": (I, [P, P, P, P]),
         "qw_autotune": (I, [P, ctypes.c_char_p, S]),
         "qw_nsites": (I64, [P]),
         "qw_describe": (I, [P, ctypes.c_char_p, S]),
@@ -214,6 +216,16 @@ def qw_get_plan(h):
     return k.value, t.value
 
 
+def qw_set_plan_ex(h, k, tile=0, variant=0):
+    _check(lib().qw_set_plan_ex(h, int(k), int(tile), int(variant)), h)
+
+
+def qw_get_plan_ex(h):
+    k, t, v = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().qw_get_plan_ex(h, ctypes.byref(k), ctypes.byref(t), ctypes.byref(v)), h)
+    return k.value, t.value, v.value
+
+
 def qw_autotune(h):
     buf = ctypes.create_string_buffer(512)
     _check(lib().qw_autotune(h, buf, 512), h)
@@ -332,6 +344,13 @@ class Walk:
 
     def plan(self):
         return qw_get_plan(self.h)
+
+    def set_plan_ex(self, k, tile=0, variant=0):
+        qw_set_plan_ex(self.h, k, tile, variant)
+        return self
+
+    def plan_ex(self):
+        return qw_get_plan_ex(self.h)
 
     def autotune(self):
         return qw_autotune(self.h)

@@ -244,3 +244,39 @@ def test_norm_drift_compensated_long_run(qw, theta):
     # unbiased rounding only: well inside T * u
     assert abs(w.norm() - 1) < 4096 * 2.0 ** -24 / 4
     w.close()
+
+
+SWEEP_CASES = [("f32", 512 * 37), ("f32", 512), ("bf16", 512 * 20), ("f64", 256 * 35)]
+
+
+@pytest.mark.parametrize("prec,N", SWEEP_CASES)
+@pytest.mark.parametrize("k", [2, 3, 17, 64, 127])
+@pytest.mark.parametrize("coin", ["hadamard_class", "real", "complex"])
+@pytest.mark.parametrize("shift", [0, 1])
+@pytest.mark.parametrize("adj", [False, True])
+def test_sweep_kernel(qw, prec, N, k, coin, shift, adj):
+    """The time-skewed sweep (variant 1) against the oracle: several segments, a
+    short last segment, one-chunk cycles, odd and large depths, all coin classes."""
+    C = {"hadamard_class": inputs.su2(np.pi / 4), "real": inputs.su2(0.3),
+         "complex": inputs.su2(0.3, 0.2, -0.5)}[coin]
+    T = 3 * k + 5
+    psi0 = inputs.random_state((2, N), seed=17)
+    want = oracle.evolve(psi0, C, T, shift=shift, adjoint=adj)
+    w = qw.Walk((N,), prec=prec, shift=shift).set_coin(C)
+    w.set_plan_ex(k, 0, 1)
+    assert w.plan_ex()[2] == 1 and w.describe()["path"] == "k_step1d_sweep"
+    w.set_state(psi0)
+    (w.step_adjoint if adj else w.step)(T)
+    assert maxabs(w.state(), want) < amp_tol(prec, T, k)
+    w.close()
+
+
+def test_sweep_rejected_where_it_cannot_run(qw):
+    w = qw.Walk((1000,), prec="f32").set_coin(inputs.hadamard())
+    with pytest.raises(qw.QWError):
+        w.set_plan_ex(16, 0, 1)          # 1000 is not a multiple of 512
+    w.close()
+    w = qw.Walk((1024,), prec="comp").set_coin(inputs.hadamard())
+    with pytest.raises(qw.QWError):
+        w.set_plan_ex(16, 0, 1)          # no sweep kernel for the double-float form
+    w.close()
