@@ -1,0 +1,164 @@
+// k_step2d_tb.cuh -- temporal blocking on the torus: KT walk steps per HBM
+// round trip, by streaming rows through a pipeline of KT time levels.
+//
+// The step is the 2D walk of Sec. 2.2 / Sec. 3 (U = S (C (x) I)): with
+// phi = C psi at every site, the moving shift gives
+//     psi'(x, y, 0) = phi(x-1, y, 0)   psi'(x, y, 1) = phi(x+1, y, 1)
+//     psi'(x, y, 2) = phi(x, y-1, 2)   psi'(x, y, 3) = phi(x, y+1, 3)
+// (flip-flop: the same values land in planes 1, 0, 3, 2).  Level s of the
+// pipeline produces row r of psi_s once level s-1 has produced row r+1, so
+// level s runs one row behind level s-1.  Each level keeps, per column, the
+// coin outputs of planes 0..2 of its input's previous row and plane 2 of the
+// row before: four complex numbers of delay line per level and column, all in
+// registers.  A warp owns a strip of 32R columns (R per lane) and a chunk of H
+// rows; planes 0 and 1 cross lane boundaries with one shuffle each, so the
+// valid columns shrink by one per level on both sides (KT columns of halo per
+// side, recomputed by the neighbouring strip) and the chunk needs KT rows of
+// warm-up below and above.  HBM traffic: one read and one write of the 4
+// planes per KT steps, plus the halo.
+#pragma once
+#include "qw_internal.cuh"
+#include "k_step2d.cuh"
+#include "k_step1d.cuh"   // wrap_index
+
+namespace qw {
+
+// Site-free coin for the streaming kernel (global coins only).
+template <int CK, class R>
+__device__ __forceinline__ void coin4g(const CoinP<R> &cp, const Cx<R> (&a)[4], Cx<R> (&p)[4]) {
+    SiteCoin<R> sc;
+    coin4<CK, R>(cp, (const Cx<R> *)nullptr, sc, a, p);
+}
+
+template <int P, int KT, int CK, int FF>
+__global__ void __launch_bounds__(128)
+k_step2d_tb(View in, View out, int64_t nx, int64_t ny, int64_t W, int64_t nstrips, int64_t H, int64_t nchunks,
+            CoinP<typename St<P>::real> cp, typename St<P>::real gain) {
+    using S = St<P>;
+    using real = typename S::real;
+    using C = Cx<real>;
+    constexpr int R = 2;   // sites per lane (one 16-byte vector per plane in FP32)
+    static_assert(R % S::VEC == 0 || S::VEC % R == 0, "lane run and vector width must nest");
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw >= nstrips * nchunks) return;   // uniform per warp
+    const int64_t strip = gw % nstrips, chunk = gw / nstrips;
+    const int64_t xo = strip * W;                       // first output column
+    const int wthis = (int)min(W, nx - xo);
+    const int64_t y0 = chunk * H;
+    const int64_t hthis = min(H, ny - y0);
+    const int j0 = lane * R;                            // tile column of the lane's first site
+    const int64_t xs = xo - KT + j0;                    // its global column (may wrap)
+    const bool vec = (xs >= 0) && (xs + R <= nx) && (xs % S::VEC == 0) && (R % S::VEC == 0);
+    int64_t cx[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) cx[i] = wrap_index(xs + i, nx);
+
+    C A[KT][R][3];   // level s input's previous row: coin outputs of planes 0, 1, 2
+    C B[KT][R];      // plane 2 from the row before that
+#pragma unroll
+    for (int s = 0; s < KT; ++s)
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            B[s][i] = czero<real>();
+#pragma unroll
+            for (int c = 0; c < 3; ++c) A[s][i][c] = czero<real>();
+        }
+    const bool gain_one = is_one(gain);
+
+    // psi_0 of the next row is loaded one iteration ahead, so its latency hides
+    // behind the KT levels of the current row
+    auto load_row = [&](int64_t q, C (&a)[4][R]) {
+        const int64_t row = wrap_index(q, ny) * nx;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (vec) {
+#pragma unroll
+                for (int i = 0; i < R; i += S::VEC) S::ldv(in, c, row + xs + i, &a[c][i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < R; ++i) a[c][i] = S::ld(in, c, row + cx[i]);
+            }
+        }
+    };
+    C nxt[4][R];
+    load_row(y0 - KT, nxt);
+    for (int64_t q = y0 - KT; q < y0 + hthis + KT; ++q) {
+        // psi_0 of row q with the coin applied: the newest input of level 1
+        C N[R][4];
+        {
+            C a[4][R];
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int i = 0; i < R; ++i) a[c][i] = nxt[c][i];
+            if (q + 1 < y0 + hthis + KT) load_row(q + 1, nxt);
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                C ai[4] = {a[0][i], a[1][i], a[2][i], a[3][i]}, pi[4];
+                coin4g<CK, real>(cp, ai, pi);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) N[i][c] = gain_one ? pi[c] : rmul(gain, pi[c]);
+            }
+        }
+        // levels 1..KT: level s produces psi_s of row q - s
+        C psi[R][4];
+#pragma unroll
+        for (int s = 0; s < KT; ++s) {
+            // x-moving planes of the previous row (A), from the neighbouring columns
+            C fl = shfl_up(A[s][R - 1][0], 1);      // coin 0 arrives from x-1
+            C fr = shfl_down(A[s][0][1], 1);        // coin 1 arrives from x+1
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const C m0 = i == 0 ? fl : A[s][i - 1][0];
+                const C m1 = i == R - 1 ? fr : A[s][i + 1][1];
+                const C m2 = B[s][i];               // coin 2 arrives from the row below
+                const C m3 = N[i][3];               // coin 3 arrives from the row above
+                psi[i][FF ? 1 : 0] = m0;
+                psi[i][FF ? 0 : 1] = m1;
+                psi[i][FF ? 3 : 2] = m2;
+                psi[i][FF ? 2 : 3] = m3;
+            }
+            // rotate this level's delay line (after every column has read it)
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                B[s][i] = A[s][i][2];
+                A[s][i][0] = N[i][0];
+                A[s][i][1] = N[i][1];
+                A[s][i][2] = N[i][2];
+            }
+            if (s + 1 < KT) {
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    C pi[4];
+                    coin4g<CK, real>(cp, psi[i], pi);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) N[i][c] = gain_one ? pi[c] : rmul(gain, pi[c]);
+                }
+            }
+        }
+        // psi_KT of row q - KT: store the columns whose light cone stayed inside the strip
+        const int64_t r = q - KT;
+        if (r >= y0) {
+            const int64_t orow = wrap_index(r, ny) * nx;
+            if (j0 >= KT && j0 + R <= KT + wthis && vec) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    C v[R];
+#pragma unroll
+                    for (int i = 0; i < R; ++i) v[i] = psi[i][c];
+#pragma unroll
+                    for (int i = 0; i < R; i += S::VEC) S::stv(out, c, orow + xs + i, &v[i]);
+                }
+            } else if (j0 + R > KT && j0 < KT + wthis) {
+#pragma unroll
+                for (int i = 0; i < R; ++i)
+                    if (j0 + i >= KT && j0 + i < KT + wthis)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) S::st(out, c, orow + cx[i], psi[i][c]);
+            }
+        }
+    }
+}
+
+}  // namespace qw

@@ -112,7 +112,11 @@ static void tiles_of(int prec, int &a, int &b) {
 
 static void default_plan(const qw_walk *w, int &k, int &tile, int &variant) {
     variant = 0;
-    if (w->ndim == 2) { k = 1; tile = 0; return; }
+    if (w->ndim == 2) {
+        tile = 0;
+        k = (w->bc == QW_BC_PERIODIC && !w->has_links && step2d_tb_ok(w->prec, w->kind, 8)) ? 8 : 1;
+        return;
+    }
     switch (w->prec) {
         case QW_F64: tile = 8; k = 8; break;
         case QW_F32_COMP: tile = 4; k = 8; break;
@@ -229,6 +233,17 @@ static double drift_gain(qw_walk *w, int steps, bool update = true) {
     return feedback_gain(w, std::pow(w->coin_alpha, -(double)steps), update);
 }
 
+// Per-step factor that one launch applies `steps` times (the 2D streaming
+// kernel), chosen with the same error feedback as feedback_gain.
+static double drift_gain_per_step(qw_walk *w, int steps) {
+    if (w->kind == CK_PERSITE || w->kind == CK_PHASE || w->coin_alpha == 1.0) return 1.0;
+    const double ideal = 1.0 / w->coin_alpha;
+    const double want = ideal * std::pow(w->gain_fb, -1.0 / steps);
+    const double g = rounds_to_float(w) ? (double)(float)want : want;
+    w->gain_fb *= std::pow(g / ideal, (double)steps);
+    return g;
+}
+
 // Pre / post per-plane factors of one 1D launch of K steps.
 static void launch_gains_1d(qw_walk *w, int K, int adj, Step1DArgs &a, bool update = true) {
     if (w->kind == CK_SIGN_P || w->kind == CK_SIGN_M) {
@@ -306,6 +321,20 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
     Step2DArgs a{};
     a.nx = w->nx; a.ny = w->ny; a.shift = w->shift; a.kind = w->kind; a.coins = w->coins_dev;
     a.phi = w->phi_dev; a.K = 1;
+    int K2, t2;
+    effective_plan(w, K2, t2);
+    if (!adj && K2 > 1 && step2d_tb_ok(w->prec, w->kind, K2)) {
+        // whole blocks of K2 steps in the streaming kernel, the rest one step at a time
+        Step2DArgs b = a;
+        b.K = K2;
+        while (T >= K2) {
+            b.gain = drift_gain_per_step(w, K2);   // applied at each of the K2 steps (1 for Grover / H(x)H)
+            b.in = cur_view(w); b.out = next_view(w);
+            if ((e = launch_step2d_tb(b, cp, w->stream)) != cudaSuccess) return cuda_error(w, e, "2D blocked step launch");
+            w->cur ^= 1;
+            T -= K2;
+        }
+    }
     for (int64_t t = 0; t < T; ++t) {
         a.gain = drift_gain(w, 1);
         a.in = cur_view(w); a.out = next_view(w);
@@ -630,8 +659,9 @@ qw_status qw_set_plan(qw_walk *w, int depth_k, int tile) {
     if (depth_k == 0) { w->plan_k = 0; w->plan_tile = 0; w->plan_user = false; return QW_OK; }
     if (depth_k < 0 || tile < 0) return set_error(w, QW_EINVAL, "negative plan");
     if (w->ndim == 2) {
-        if (depth_k != 1) return set_error(w, QW_EUNSUPPORTED, "2D plans take k = 1");
-        w->plan_k = 1; w->plan_tile = 0; w->plan_user = true;
+        if (depth_k != 1 && depth_k != 4 && depth_k != 8)
+            return set_error(w, QW_EINVAL, "2D plans take k = 1, 4 or 8");
+        w->plan_k = depth_k; w->plan_tile = 0; w->plan_user = true;
         return QW_OK;
     }
     int dk, dt, dv;
@@ -683,7 +713,9 @@ qw_status qw_describe(const qw_walk *w, char *buf, size_t len) {
                   "{\"ndim\": %d, \"sites\": %lld, \"coin_dim\": %d, \"precision\": %d, \"coin_kind\": \"%s\", "
                   "\"k\": %d, \"tile\": %d, \"path\": \"%s\", \"state_bytes\": %zu}",
                   w->ndim, (long long)w->ns, w->d, w->prec, kinds[w->kind], k, t,
-                  generic ? "generic" : (w->ndim == 1 ? (var == 1 ? "k_step1d_sweep" : "k_step1d") : "k_step2d"),
+                  generic ? "generic"
+                          : (w->ndim == 1 ? (var == 1 ? "k_step1d_sweep" : "k_step1d")
+                                          : (k > 1 && step2d_tb_ok(w->prec, w->kind, k) ? "k_step2d_tb" : "k_step2d")),
                   w->state_bytes);
     return QW_OK;
 }
@@ -753,8 +785,42 @@ extern "C" qw_status qw_autotune(qw_walk *w, char *report, size_t report_len) {
     auto put = [&](const char *s) {
         if (report && report_len) { std::strncpy(report, s, report_len - 1); report[report_len - 1] = 0; }
     };
-    if (w->ndim != 1 || w->bc != QW_BC_PERIODIC || w->has_links) {
-        put("{\"tuned\": false, \"reason\": \"only the periodic 1D kernel has a plan space\"}");
+    if (w->bc != QW_BC_PERIODIC || w->has_links) {
+        put("{\"tuned\": false, \"reason\": \"the generic boundary / broken-link kernel has no plan space\"}");
+        return QW_OK;
+    }
+    if (w->ndim == 2) {
+        // k = 1 (fused step) against the streaming kernel at k = 4 and 8
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        Step2DArgs a{};
+        a.nx = w->nx; a.ny = w->ny; a.shift = w->shift; a.kind = w->kind; a.coins = w->coins_dev;
+        a.phi = w->phi_dev; a.gain = 1.0;
+        a.in = cur_view(w); a.out = next_view(w);
+        float best = 1e30f;
+        int best_k = 1;
+        cudaError_t err = cudaSuccess;
+        for (int k : {1, 4, 8}) {
+            if (k > 1 && !step2d_tb_ok(w->prec, w->kind, k)) continue;
+            a.K = k;
+            auto launch = [&]() { return k == 1 ? step2d(w->prec, a, w->coinp, 0, w->stream) : launch_step2d_tb(a, w->coinp, w->stream); };
+            if ((err = launch()) != cudaSuccess) break;
+            cudaEventRecord(e0, w->stream);
+            for (int r = 0; r < 3; ++r) launch();
+            cudaEventRecord(e1, w->stream);
+            if ((err = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms / (3 * k) < best) { best = ms / (3 * k); best_k = k; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (err != cudaSuccess) return cuda_error(w, err, "autotune");
+        w->plan_k = best_k; w->plan_tile = 0; w->plan_user = true;
+        char b2[256];
+        std::snprintf(b2, sizeof b2, "{\"tuned\": true, \"ndim\": 2, \"k\": %d, \"ms_per_step\": %.6g}", best_k, best);
+        put(b2);
         return QW_OK;
     }
     std::lock_guard<std::mutex> lock(g_tune_mu);

@@ -97,6 +97,10 @@ int tile1d_f64(int, int, int);
 int tile1d_bf16(int, int, int);
 int tile1d_comp(int, int, int);
 
+// streaming temporal blocking on the torus (step2d_tb.cu)
+bool step2d_tb_ok(int prec, int kind, int K);
+cudaError_t launch_step2d_tb(const Step2DArgs &a, const void *coinp, cudaStream_t s);
+
 // per-site coin conversion kernels (qw_coins.cu)
 cudaError_t launch_convert_coins(int prec, const double *src, void *dst, int64_t count, cudaStream_t s);
 cudaError_t launch_phase_coins(int prec, const double *base, const float *phi, void *dst, int64_t ns,
