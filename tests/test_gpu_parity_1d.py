@@ -182,8 +182,9 @@ def test_autotune_keeps_state_and_picks_a_valid_plan(qw):
     w = qw.Walk((N,), prec="f32").set_coin(inputs.su2(np.pi / 4)).set_state(psi0)
     rep = w.autotune()
     assert '"tuned": true' in rep
-    k, tile = w.plan()
-    assert 1 <= k <= 8 * tile
+    k, tile, variant = w.plan_ex()
+    # the tile kernel takes k <= 8 * tile; the sweep kernel k < chunk / 2 = 16 * tile
+    assert 1 <= k <= (8 * tile if variant == 0 else 16 * tile - 1)
     assert maxabs(w.state(), psi0) < 1e-7   # tuning wrote only the scratch buffer
     w.close()
 
