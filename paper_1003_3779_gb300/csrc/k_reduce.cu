@@ -6,7 +6,12 @@
 // sites, a block reduces its threads with warp shuffles, and a second one-block
 // kernel adds the per-block partials in block order.  The grid size is fixed,
 // so the summation order, and hence every bit of the result, does not depend
-// on timing.
+// on timing.  For float amplitudes with a float P the per-site sum of squares
+// is formed in float (one rounding of 2^-24 per site) and only the running
+// norm is double: double arithmetic runs at a small fraction of the float rate
+// on this part.
+#include <type_traits>
+
 #include "qw_internal.cuh"
 
 namespace qw {
@@ -44,6 +49,28 @@ k_marginals(View v, int64_t ns, void *P_out, double *partials) {
         double p[S::VEC];
 #pragma unroll
         for (int k = 0; k < S::VEC; ++k) p[k] = 0.0;
+        if constexpr (PF32 && std::is_same<real, float>::value) {
+          if (i0 + S::VEC <= ns) {
+            // float amplitudes and a float P: |psi|^2 per site in float (FP64 is
+            // slow on this part), the VEC sites summed in float, one double add
+            float pf[S::VEC], grp = 0.f;
+#pragma unroll
+            for (int k = 0; k < S::VEC; ++k) pf[k] = 0.f;
+            for (int c = 0; c < d; ++c) {
+                Cx<real> a[S::VEC];
+                S::ldv(v, c, i0, a);
+#pragma unroll
+                for (int k = 0; k < S::VEC; ++k) pf[k] = __fmaf_rn((float)a[k].re, (float)a[k].re, __fmaf_rn((float)a[k].im, (float)a[k].im, pf[k]));
+            }
+#pragma unroll
+            for (int k = 0; k < S::VEC; ++k) {
+                grp += pf[k];
+                if (P_out) reinterpret_cast<float *>(P_out)[i0 + k] = pf[k];
+            }
+            acc += (double)grp;
+            continue;
+          }
+        }
         if (i0 + S::VEC <= ns) {
             for (int c = 0; c < d; ++c) {
                 Cx<real> a[S::VEC];
