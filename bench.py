@@ -179,7 +179,7 @@ def cpu_oracle_sample(target_s=12.0):
 # ------------------------------------------------------------------ GPU arm
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("k_step1d.cuh", "qw_internal.cuh", "launch_step.cuh"):  # every 1D step kernel lives here
+    for f in ("k_step1d.cuh", "qw_internal.cuh"):   # the device code of every 1D step kernel
         h.update(open(os.path.join(ROOT, "paper_1003_3779_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

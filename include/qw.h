@@ -19,7 +19,8 @@
  *     2D coin 0: +x, 1: -x, 2: +y, 3: -y.  (The paper's own labelling of the
  *     2D shift equation in Sec. 3 is a permutation of this basis.)
  *   - moving shift:    S|v,c> = |v + e_c, c>;
- *     flip-flop shift: S|v,c> = |v + e_c, c xor 1>.
+ *     flip-flop shift: S|v,c> = |v + e_c, c xor 1>;
+ *     diagonal lattice (2D): S|v,c> = |v + d_c, c>, d_c = ((-1)^j, (-1)^k), c = 2j+k.
  *   - a closed link (broken link, Sec. 3 "RBL") reflects: the amplitude stays
  *     on its site, in coin c xor 1 (moving) or c (flip-flop).
  *   - state layout seen by callers: d coin-major planes of nsites complex
@@ -68,7 +69,10 @@ typedef enum {
     QW_BC_LINE = 2        /* finite window of the infinite line: amplitude crossing the edge is dropped (Sec. 3 "line") */
 } qw_boundary;
 
-typedef enum { QW_SHIFT_MOVING = 0, QW_SHIFT_FLIPFLOP = 1 } qw_shift;
+/* Shift S (Sec. 2.1, Sec. 3).  QW_SHIFT_DIAGONAL is the diagonal lattice of
+ * Sec. 3 (Fig. 1(c)) on the torus: each coin qubit drives one axis, coin
+ * c = 2j+k moves the walker by ((-1)^j, (-1)^k); 2D, periodic, no broken links. */
+typedef enum { QW_SHIFT_MOVING = 0, QW_SHIFT_FLIPFLOP = 1, QW_SHIFT_DIAGONAL = 2 } qw_shift;
 
 /* Storage / arithmetic of the state.  QW_F64: double storage and arithmetic.
  * QW_F32: float.  QW_F32_BF16STORE: bfloat16 storage, float arithmetic (one

@@ -30,7 +30,7 @@ _LIBS: dict = {}
 _LOCK = threading.Lock()
 
 BC_PERIODIC, BC_SEGMENT, BC_LINE = 0, 1, 2
-SHIFT_MOVING, SHIFT_FLIPFLOP = 0, 1
+SHIFT_MOVING, SHIFT_FLIPFLOP, SHIFT_DIAGONAL = 0, 1, 2
 
 
 def build(openmp: bool = False) -> str:

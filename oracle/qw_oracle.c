@@ -24,6 +24,9 @@
  *   - 2D directions: coin 0: +x, 1: -x, 2: +y, 3: -y;
  *   - moving shift:    S|v,c> = |v + e_c, c>
  *     flip-flop shift: S|v,c> = |v + e_c, c xor 1>
+ *     diagonal lattice (2D, Sec. 3 Fig. 1(c)): each coin qubit drives one axis,
+ *     coin c = 2j+k moves by ((-1)^j, (-1)^k): S|v,c> = |v + d_c, c>
+ *     (periodic torus only, no broken links)
  *   - a closed link (RBL) reflects: the amplitude stays on its site and
  *     takes the one coin slot the closed link leaves empty, which keeps S a
  *     permutation of basis states: S|v,c> = |v, c xor 1> for the moving
@@ -56,7 +59,7 @@ typedef struct {
     int64_t nx, ny;    /* extent in x and y (ny = 1 in 1D) */
     int64_t nsites;    /* nx * ny */
     int d;             /* coin dimension: 2 (1D) or 4 (2D) */
-    int shift;         /* 0 moving, 1 flip-flop */
+    int shift;         /* 0 moving, 1 flip-flop, 2 diagonal lattice (2D) */
     int bc;            /* 0 periodic, 1 segment (reflect), 2 line (absorb) */
     const uint8_t *closed; /* NULL, or ndim*nsites link flags (RBL) */
     int coin_mode;     /* 0 global, 1 per-site matrices, 2 per-site phases */
@@ -70,7 +73,8 @@ static int lattice_init(lattice *L, int ndim, const int64_t *dims, int shift,
 {
     if (ndim != 1 && ndim != 2) return OR_EINVAL;
     if (!dims || dims[0] < 1 || (ndim == 2 && dims[1] < 1)) return OR_EINVAL;
-    if (shift != 0 && shift != 1) return OR_EINVAL;
+    if (shift < 0 || shift > 2) return OR_EINVAL;
+    if (shift == 2 && (ndim != 2 || bc != 0 || closed)) return OR_EINVAL;
     if (bc < 0 || bc > 2) return OR_EINVAL;
     if (coin_mode < 0 || coin_mode > 2 || !coin) return OR_EINVAL;
     if (coin_mode == 2 && !phi) return OR_EINVAL;
@@ -117,6 +121,13 @@ static void coin_at(const lattice *L, int64_t v, cplx *C)
 static int shift_map(const lattice *L, int64_t v, int c, int64_t *vo, int *co)
 {
     int64_t x = v % L->nx, y = v / L->nx;
+    if (L->shift == 2) {   /* diagonal lattice: coin c = 2j+k moves by ((-1)^j, (-1)^k) */
+        int64_t dx = (c >> 1) ? -1 : 1, dy = (c & 1) ? -1 : 1;
+        int64_t xn = (x + dx + L->nx) % L->nx, yn = (y + dy + L->ny) % L->ny;
+        *vo = yn * L->nx + xn;
+        *co = c;
+        return 1;
+    }
     int axis, sgn;
     if (L->ndim == 1) { axis = 0; sgn = (c == 0) ? -1 : +1; }
     else { axis = c >> 1; sgn = (c & 1) ? -1 : +1; }

@@ -95,6 +95,31 @@ k_step_generic(View in, View out, GenGeom g, int adjoint, CoinP<typename St<P>::
     const int d = 2 * g.ndim;
     const int64_t x = v % g.nx, y = v / g.nx;
     C e[4];
+    if (g.shift == 2) {   // diagonal lattice (periodic torus): coin c moves by d_c
+        if (!adjoint) {
+            for (int co = 0; co < 4; ++co) {
+                const int64_t ux = (x - dir_dx<2>(co) + g.nx) % g.nx, uy = (y - dir_dy<2>(co) + g.ny) % g.ny;
+                const int64_t u = uy * g.nx + ux;
+                if (CK == CK_PHASE) gen_phases<real>(phi, u, d, e);
+                C val = czero<real>();
+                for (int k = 0; k < d; ++k) val = cfma(gen_entry<CK, real>(cp, coins, e, d, u, co, k), S::ld(in, k, u), val);
+                S::st(out, co, v, rmul(gain, val));
+            }
+        } else {
+            C b[4];
+            for (int c = 0; c < 4; ++c) {
+                const int64_t tx = (x + dir_dx<2>(c) + g.nx) % g.nx, ty = (y + dir_dy<2>(c) + g.ny) % g.ny;
+                b[c] = S::ld(in, c, ty * g.nx + tx);
+            }
+            if (CK == CK_PHASE) gen_phases<real>(phi, v, d, e);
+            for (int k = 0; k < d; ++k) {
+                C acc = czero<real>();
+                for (int r = 0; r < d; ++r) acc = cadd(acc, conjmul(gen_entry<CK, real>(cp, coins, e, d, v, r, k), b[r]));
+                S::st(out, k, v, rmul(gain, acc));
+            }
+        }
+        return;
+    }
     if (!adjoint) {
         for (int co = 0; co < d; ++co) {
             // which (u, c) lands in (v, co)?

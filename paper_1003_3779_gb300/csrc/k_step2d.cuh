@@ -143,13 +143,20 @@ __device__ __forceinline__ void site_coin(const float *phi, int64_t v, SiteCoin<
     if (needs_phase<CK>()) phase_of(phi, v, sc);
 }
 
-// Displacement of coin c: 0 +x, 1 -x, 2 +y, 3 -y.
-__device__ __forceinline__ int dir_dx(int c) { return c == 0 ? 1 : (c == 1 ? -1 : 0); }
-__device__ __forceinline__ int dir_dy(int c) { return c == 2 ? 1 : (c == 3 ? -1 : 0); }
+// Displacement of coin c: 0 +x, 1 -x, 2 +y, 3 -y; on the diagonal lattice
+// (SH = 2) coin c = 2j+k moves by ((-1)^j, (-1)^k).
+template <int SH> __device__ __forceinline__ int dir_dx(int c) {
+    if (SH == 2) return (c >> 1) ? -1 : 1;
+    return c == 0 ? 1 : (c == 1 ? -1 : 0);
+}
+template <int SH> __device__ __forceinline__ int dir_dy(int c) {
+    if (SH == 2) return (c & 1) ? -1 : 1;
+    return c == 2 ? 1 : (c == 3 ? -1 : 0);
+}
 
 // Ragged segment (fewer than 32R sites left in the row): one site per lane
 // iteration in plain pull form, recomputing the source site's coin.
-template <int P, int CK, int FF, int ADJ>
+template <int P, int CK, int SH, int ADJ>
 __device__ void step2d_site(View in, View out, int64_t nx, int64_t ny, int64_t x, int64_t y,
                             const CoinP<typename St<P>::real> &cp, const float *phi,
                             const Cx<typename St<P>::real> *coins, typename St<P>::real gain) {
@@ -160,8 +167,8 @@ __device__ void step2d_site(View in, View out, int64_t nx, int64_t ny, int64_t x
     if (!ADJ) {
 #pragma unroll
         for (int co = 0; co < 4; ++co) {
-            const int c = FF ? (co ^ 1) : co;  // coin that lands in plane co
-            const int64_t ux = (x - dir_dx(c) + nx) % nx, uy = (y - dir_dy(c) + ny) % ny;
+            const int c = SH == 1 ? (co ^ 1) : co;  // coin that lands in plane co
+            const int64_t ux = (x - dir_dx<SH>(c) + nx) % nx, uy = (y - dir_dy<SH>(c) + ny) % ny;
             const int64_t u = uy * nx + ux;
             C a[4], p[4];
 #pragma unroll
@@ -175,8 +182,8 @@ __device__ void step2d_site(View in, View out, int64_t nx, int64_t ny, int64_t x
         C b[4], a[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const int64_t ux = (x + dir_dx(c) + nx) % nx, uy = (y + dir_dy(c) + ny) % ny;
-            b[c] = S::ld(in, FF ? (c ^ 1) : c, uy * nx + ux);
+            const int64_t ux = (x + dir_dx<SH>(c) + nx) % nx, uy = (y + dir_dy<SH>(c) + ny) % ny;
+            b[c] = S::ld(in, SH == 1 ? (c ^ 1) : c, uy * nx + ux);
         }
         SiteCoin<real> sc;
         site_coin<P, CK>(phi, v, sc);
@@ -186,7 +193,7 @@ __device__ void step2d_site(View in, View out, int64_t nx, int64_t ny, int64_t x
     }
 }
 
-template <int P, int R, int CK, int FF, int ADJ>
+template <int P, int R, int CK, int SH, int ADJ>
 __global__ void __launch_bounds__(128)
 k_step2d(View in, View out, int64_t nx, int64_t ny, int64_t segs, int64_t nwarps,
          CoinP<typename St<P>::real> cp, const float *__restrict__ phi,
@@ -205,7 +212,7 @@ k_step2d(View in, View out, int64_t nx, int64_t ny, int64_t segs, int64_t nwarps
     if (x0 + 32 * R > nx) {  // ragged tail of the row (uniform per warp)
 #pragma unroll 1
         for (int i = 0; i < R; ++i)
-            if (xs + i < nx) step2d_site<P, CK, FF, ADJ>(in, out, nx, ny, xs + i, y, cp, phi, coins, gain);
+            if (xs + i < nx) step2d_site<P, CK, SH, ADJ>(in, out, nx, ny, xs + i, y, cp, phi, coins, gain);
         return;
     }
     const int64_t yp = (y + 1 == ny) ? 0 : y + 1;
@@ -239,6 +246,51 @@ k_step2d(View in, View out, int64_t nx, int64_t ny, int64_t segs, int64_t nwarps
 #pragma unroll
                 for (int c = 0; c < 4; ++c) p[c][i] = rmul(gain, p[c][i]);
         }
+        if constexpr (SH == 2) {
+            // diagonal lattice: coins 0, 1 arrive from x-1, coins 2, 3 from x+1;
+            // coins 0, 2 go to row y+1, coins 1, 3 to row y-1
+            C ha = czero<real>(), hb = czero<real>();
+            if (lane == 0 || lane == 31) {
+                const int64_t xh = (lane == 0) ? (x0 == 0 ? nx - 1 : x0 - 1) : ((x0 + 32 * R) % nx);
+                C ah[4], ph[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) ah[c] = S::ld(in, c, row + xh);
+                SiteCoin<real> sc;
+                site_coin<P, CK>(phi, row + xh, sc);
+                coin4<CK, real>(cp, coins + 16 * (row + xh), sc, ah, ph);
+                ha = rmul(gain, lane == 0 ? ph[0] : ph[2]);
+                hb = rmul(gain, lane == 0 ? ph[1] : ph[3]);
+            }
+            C f0 = shfl_up(p[0][R - 1], 1), f1 = shfl_up(p[1][R - 1], 1);
+            C f2 = shfl_down(p[2][0], 1), f3 = shfl_down(p[3][0], 1);
+            if (lane == 0) { f0 = ha; f1 = hb; }
+            if (lane == 31) { f2 = ha; f3 = hb; }
+            C m0[R], m1[R], m2[R], m3[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                m0[i] = (i == 0) ? f0 : p[0][i - 1];
+                m1[i] = (i == 0) ? f1 : p[1][i - 1];
+                m2[i] = (i == R - 1) ? f2 : p[2][i + 1];
+                m3[i] = (i == R - 1) ? f3 : p[3][i + 1];
+            }
+            if (vec_ok) {
+#pragma unroll
+                for (int i = 0; i < R; i += S::VEC) {
+                    S::stv(out, 0, yp * nx + xs + i, &m0[i]);
+                    S::stv(out, 1, ym * nx + xs + i, &m1[i]);
+                    S::stv(out, 2, yp * nx + xs + i, &m2[i]);
+                    S::stv(out, 3, ym * nx + xs + i, &m3[i]);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    S::st(out, 0, yp * nx + xs + i, m0[i]);
+                    S::st(out, 1, ym * nx + xs + i, m1[i]);
+                    S::st(out, 2, yp * nx + xs + i, m2[i]);
+                    S::st(out, 3, ym * nx + xs + i, m3[i]);
+                }
+            }
+        } else {
         // coin 0 of the site left of the segment, coin 1 of the site right of it
         C halo = czero<real>();
         if (lane == 0 || lane == 31) {
@@ -261,7 +313,7 @@ k_step2d(View in, View out, int64_t nx, int64_t ny, int64_t segs, int64_t nwarps
             m0[i] = (i == 0) ? fl : p[0][i - 1];      // arrived from x-1 (coin 0 moves +x)
             m1[i] = (i == R - 1) ? fr : p[1][i + 1];  // arrived from x+1 (coin 1 moves -x)
         }
-        const int o0 = FF ? 1 : 0, o1 = FF ? 0 : 1, o2 = FF ? 3 : 2, o3 = FF ? 2 : 3;
+        const int o0 = SH ? 1 : 0, o1 = SH ? 0 : 1, o2 = SH ? 3 : 2, o3 = SH ? 2 : 3;
         if (vec_ok) {
 #pragma unroll
             for (int i = 0; i < R; i += S::VEC) {
@@ -279,9 +331,47 @@ k_step2d(View in, View out, int64_t nx, int64_t ny, int64_t segs, int64_t nwarps
                 S::st(out, o3, ym * nx + xs + i, p[3][i]);
             }
         }
+        }
     } else {
         // S^dagger: b_c(x, y) = psi_{src c}(x + e_c)
-        const int s0 = FF ? 1 : 0, s1 = FF ? 0 : 1, s2 = FF ? 3 : 2, s3 = FF ? 2 : 3;
+        C bb0[R], bb1[R], bb2[R], bb3[R];
+        if constexpr (SH == 2) {
+            // diagonal: b0 = psi0(x+1, y+1), b1 = psi1(x+1, y-1), b2 = psi2(x-1, y+1), b3 = psi3(x-1, y-1)
+            C r0[R], r1[R], r2[R], r3[R];
+            if (vec_ok) {
+#pragma unroll
+                for (int i = 0; i < R; i += S::VEC) {
+                    S::ldv(in, 0, yp * nx + xs + i, &r0[i]);
+                    S::ldv(in, 1, ym * nx + xs + i, &r1[i]);
+                    S::ldv(in, 2, yp * nx + xs + i, &r2[i]);
+                    S::ldv(in, 3, ym * nx + xs + i, &r3[i]);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    r0[i] = S::ld(in, 0, yp * nx + xs + i);
+                    r1[i] = S::ld(in, 1, ym * nx + xs + i);
+                    r2[i] = S::ld(in, 2, yp * nx + xs + i);
+                    r3[i] = S::ld(in, 3, ym * nx + xs + i);
+                }
+            }
+            const int64_t xr = (x0 + 32 * R) % nx, xl = x0 == 0 ? nx - 1 : x0 - 1;
+            C ha = czero<real>(), hb = czero<real>();
+            if (lane == 31) { ha = S::ld(in, 0, yp * nx + xr); hb = S::ld(in, 1, ym * nx + xr); }
+            if (lane == 0) { ha = S::ld(in, 2, yp * nx + xl); hb = S::ld(in, 3, ym * nx + xl); }
+            C g0 = shfl_down(r0[0], 1), g1 = shfl_down(r1[0], 1);
+            C g2 = shfl_up(r2[R - 1], 1), g3 = shfl_up(r3[R - 1], 1);
+            if (lane == 31) { g0 = ha; g1 = hb; }
+            if (lane == 0) { g2 = ha; g3 = hb; }
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                bb0[i] = (i == R - 1) ? g0 : r0[i + 1];
+                bb1[i] = (i == R - 1) ? g1 : r1[i + 1];
+                bb2[i] = (i == 0) ? g2 : r2[i - 1];
+                bb3[i] = (i == 0) ? g3 : r3[i - 1];
+            }
+        } else {
+        const int s0 = SH ? 1 : 0, s1 = SH ? 0 : 1, s2 = SH ? 3 : 2, s3 = SH ? 2 : 3;
         C r0[R], r1[R], b2[R], b3[R];
         if (vec_ok) {
 #pragma unroll
@@ -307,10 +397,18 @@ k_step2d(View in, View out, int64_t nx, int64_t ny, int64_t segs, int64_t nwarps
         C fl = shfl_up(r1[R - 1], 1);
         if (lane == 31) fr = halo;
         if (lane == 0) fl = halo;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            bb0[i] = (i == R - 1) ? fr : r0[i + 1];
+            bb1[i] = (i == 0) ? fl : r1[i - 1];
+            bb2[i] = b2[i];
+            bb3[i] = b3[i];
+        }
+        }
         C res[4][R];
 #pragma unroll
         for (int i = 0; i < R; ++i) {
-            C bi[4] = {(i == R - 1) ? fr : r0[i + 1], (i == 0) ? fl : r1[i - 1], b2[i], b3[i]}, ai[4];
+            C bi[4] = {bb0[i], bb1[i], bb2[i], bb3[i]}, ai[4];
             SiteCoin<real> sc;
             site_coin<P, CK>(phi, row + xs + i, sc);
             coin4_adj<CK, real>(cp, coins + 16 * (row + xs + i), sc, bi, ai);

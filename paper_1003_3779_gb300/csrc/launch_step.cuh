@@ -197,9 +197,11 @@ static void go2d(const Step2DArgs &a, const CoinP<typename St<P>::real> &cp, cud
 
 template <int P, int CK>
 static void go2d_ff(const Step2DArgs &a, const CoinP<typename St<P>::real> &cp, int adj, cudaStream_t s) {
-    const bool ff = a.shift == QW_SHIFT_FLIPFLOP;
-    if (!adj) ff ? go2d<P, CK, 1, 0>(a, cp, s) : go2d<P, CK, 0, 0>(a, cp, s);
-    else ff ? go2d<P, CK, 1, 1>(a, cp, s) : go2d<P, CK, 0, 1>(a, cp, s);
+    switch (a.shift) {
+        case QW_SHIFT_FLIPFLOP: adj ? go2d<P, CK, 1, 1>(a, cp, s) : go2d<P, CK, 1, 0>(a, cp, s); break;
+        case QW_SHIFT_DIAGONAL: adj ? go2d<P, CK, 2, 1>(a, cp, s) : go2d<P, CK, 2, 0>(a, cp, s); break;
+        default: adj ? go2d<P, CK, 0, 1>(a, cp, s) : go2d<P, CK, 0, 0>(a, cp, s); break;
+    }
 }
 
 // Does the fast 2D kernel of precision P handle this coin kind?

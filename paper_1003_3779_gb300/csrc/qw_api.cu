@@ -114,7 +114,7 @@ static void default_plan(const qw_walk *w, int &k, int &tile, int &variant) {
     variant = 0;
     if (w->ndim == 2) {
         tile = 0;
-        k = (w->bc == QW_BC_PERIODIC && !w->has_links && step2d_tb_ok(w->prec, w->kind, 8)) ? 8 : 1;
+        k = (w->bc == QW_BC_PERIODIC && !w->has_links && step2d_tb_ok(w->prec, w->kind, 8, w->shift)) ? 8 : 1;
         return;
     }
     switch (w->prec) {
@@ -323,7 +323,7 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
     a.phi = w->phi_dev; a.K = 1;
     int K2, t2;
     effective_plan(w, K2, t2);
-    if (!adj && K2 > 1 && step2d_tb_ok(w->prec, w->kind, K2)) {
+    if (!adj && K2 > 1 && step2d_tb_ok(w->prec, w->kind, K2, w->shift)) {
         // whole blocks of K2 steps in the streaming kernel, the rest one step at a time
         Step2DArgs b = a;
         b.K = K2;
@@ -390,8 +390,9 @@ qw_status qw_create(int ndim, const int64_t *dims, int coin_dim, qw_boundary bc,
     *out = nullptr;
     if ((ndim != 1 && ndim != 2) || !dims || coin_dim != 2 * ndim) return QW_EINVAL;
     if (dims[0] < 1 || (ndim == 2 && dims[1] < 1)) return QW_EINVAL;
-    if ((int)bc < 0 || (int)bc > 2 || (int)shift < 0 || (int)shift > 1 || (int)prec < 0 || (int)prec > 3)
+    if ((int)bc < 0 || (int)bc > 2 || (int)shift < 0 || (int)shift > 2 || (int)prec < 0 || (int)prec > 3)
         return QW_EINVAL;
+    if (shift == QW_SHIFT_DIAGONAL && (ndim != 2 || bc != QW_BC_PERIODIC)) return QW_EINVAL;
     const int64_t nx = dims[0], ny = ndim == 2 ? dims[1] : 1;
     if (nx > (int64_t(1) << 40) || ny > (int64_t(1) << 40) || nx * ny > (int64_t(1) << 40)) return QW_EINVAL;
 
@@ -518,6 +519,7 @@ qw_status qw_set_coin_phases(qw_walk *w, const double *base, const float *phi, i
 qw_status qw_set_links(qw_walk *w, const uint8_t *closed, int on_device) {
     if (!w) return QW_EINVAL;
     if (!closed) { w->has_links = false; return QW_OK; }
+    if (w->shift == QW_SHIFT_DIAGONAL) return set_error(w, QW_EUNSUPPORTED, "broken links are defined on the axis lattice");
     const size_t bytes = (size_t)w->ndim * w->ns;
     cudaError_t e;
     if (!w->links_dev && (e = dev_alloc((void **)&w->links_dev, bytes)) != cudaSuccess)
@@ -715,7 +717,7 @@ qw_status qw_describe(const qw_walk *w, char *buf, size_t len) {
                   w->ndim, (long long)w->ns, w->d, w->prec, kinds[w->kind], k, t,
                   generic ? "generic"
                           : (w->ndim == 1 ? (var == 1 ? "k_step1d_sweep" : "k_step1d")
-                                          : (k > 1 && step2d_tb_ok(w->prec, w->kind, k) ? "k_step2d_tb" : "k_step2d")),
+                                          : (k > 1 && step2d_tb_ok(w->prec, w->kind, k, w->shift) ? "k_step2d_tb" : "k_step2d")),
                   w->state_bytes);
     return QW_OK;
 }
@@ -802,7 +804,7 @@ extern "C" qw_status qw_autotune(qw_walk *w, char *report, size_t report_len) {
         int best_k = 1;
         cudaError_t err = cudaSuccess;
         for (int k : {1, 4, 8}) {
-            if (k > 1 && !step2d_tb_ok(w->prec, w->kind, k)) continue;
+            if (k > 1 && !step2d_tb_ok(w->prec, w->kind, k, w->shift)) continue;
             a.K = k;
             auto launch = [&]() { return k == 1 ? step2d(w->prec, a, w->coinp, 0, w->stream) : launch_step2d_tb(a, w->coinp, w->stream); };
             if ((err = launch()) != cudaSuccess) break;

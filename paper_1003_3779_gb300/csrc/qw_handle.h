@@ -98,7 +98,7 @@ int tile1d_bf16(int, int, int);
 int tile1d_comp(int, int, int);
 
 // streaming temporal blocking on the torus (step2d_tb.cu)
-bool step2d_tb_ok(int prec, int kind, int K);
+bool step2d_tb_ok(int prec, int kind, int K, int shift);
 cudaError_t launch_step2d_tb(const Step2DArgs &a, const void *coinp, cudaStream_t s);
 
 // per-site coin conversion kernels (qw_coins.cu)

@@ -40,8 +40,8 @@ static cudaError_t go2d_tb_kind(const Step2DArgs &a, const CoinP<float> &cp, cud
     }
 }
 
-bool step2d_tb_ok(int prec, int kind, int K) {
-    return prec == QW_F32 && (K == 4 || K == 8) &&
+bool step2d_tb_ok(int prec, int kind, int K, int shift) {
+    return prec == QW_F32 && (K == 4 || K == 8) && shift != QW_SHIFT_DIAGONAL &&
            (kind == CK_REAL || kind == CK_COMPLEX || kind == CK_GROVER || kind == CK_HH);
 }
 

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libqw.so")
 
 QW_OK, QW_EINVAL, QW_ENOMEM, QW_ECUDA, QW_ESTATE, QW_ETIMEOUT, QW_EUNSUPPORTED = range(7)
 BC_PERIODIC, BC_SEGMENT, BC_LINE = 0, 1, 2
-SHIFT_MOVING, SHIFT_FLIPFLOP = 0, 1
+SHIFT_MOVING, SHIFT_FLIPFLOP, SHIFT_DIAGONAL = 0, 1, 2
 F64, F32, F32_BF16STORE, F32_COMP = 0, 1, 2, 3
 C128, C64 = 0, 1
 R64, R32 = 0, 1

@@ -11,6 +11,20 @@ import numpy as np
 
 DIR_1D = [(-1, 0), (1, 0)]
 DIR_2D = [(1, 0), (-1, 0), (0, 1), (0, -1)]
+DIR_DIAG = [(1, 1), (1, -1), (-1, 1), (-1, -1)]
+
+
+def diagonal_shift_matrix(dims):
+    """S of the diagonal lattice (periodic): |x, y, c> -> |x + dx_c, y + dy_c, c>."""
+    Lx, Ly = dims
+    ns = Lx * Ly
+    S = np.zeros((4 * ns, 4 * ns))
+    for v in range(ns):
+        x, y = v % Lx, v // Lx
+        for c, (dx, dy) in enumerate(DIR_DIAG):
+            u = ((y + dy) % Ly) * Lx + (x + dx) % Lx
+            S[c * ns + u, c * ns + v] = 1.0
+    return S
 
 
 def shift_matrix(dims, flipflop=False, bc=0, closed=None, dirs=None):

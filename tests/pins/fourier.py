@@ -13,9 +13,10 @@ import numpy as np
 # 2D coin 0 +x, 1 -x, 2 +y, 3 -y
 DIR_1D = [(-1, 0), (1, 0)]
 DIR_2D = [(1, 0), (-1, 0), (0, 1), (0, -1)]
+DIR_DIAG = [(1, 1), (1, -1), (-1, 1), (-1, -1)]   # coin c = 2j+k moves ((-1)^j, (-1)^k)
 
 
-def evolve_fourier(psi, coin, T, flipflop=False):
+def evolve_fourier(psi, coin, T, flipflop=False, diagonal=False):
     psi = np.asarray(psi, dtype=np.complex128)
     coin = np.asarray(coin, dtype=np.complex128)
     if psi.ndim == 2:
@@ -27,7 +28,7 @@ def evolve_fourier(psi, coin, T, flipflop=False):
         spatial_shape = (N,)
     else:
         d, Ly, Lx = psi.shape
-        dirs = DIR_2D
+        dirs = DIR_DIAG if diagonal else DIR_2D
         hat = np.fft.fft2(psi, axes=(1, 2))             # (d, Ly, Lx)
         ky = np.arange(Ly)[:, None]
         kx = np.arange(Lx)[None, :]

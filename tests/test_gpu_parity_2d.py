@@ -171,3 +171,42 @@ def test_torus_temporal_blocking(qw, k, coin, shift, dims):
     w.step(T)
     assert maxabs(w.state(), want) < amp_tol("f32", T)
     w.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("coin", ["hh", "fourier", "grover", "complex"])
+@pytest.mark.parametrize("adjoint", [False, True])
+@pytest.mark.parametrize("dims", [(136, 18), (9, 7)])
+def test_diagonal_lattice(qw, prec, coin, adjoint, dims):
+    """The diagonal lattice (each coin qubit drives one axis) against the oracle,
+    forward and adjoint, full segments plus ragged tails and a tiny torus."""
+    rng = np.random.default_rng(["hh", "fourier", "grover", "complex"].index(coin) + 50)
+    C = coin_named(coin, rng)
+    Lx, Ly = dims
+    T = 21
+    psi0 = inputs.random_state((4, Ly, Lx), seed=27)
+    want = oracle.evolve(psi0, C, T, shift=2, adjoint=adjoint)
+    w = qw.Walk((Lx, Ly), prec=prec, shift=qw.SHIFT_DIAGONAL).set_coin(C).set_state(psi0)
+    (w.step_adjoint if adjoint else w.step)(T)
+    assert maxabs(w.state(), want) < amp_tol(prec, T)
+    w.close()
+
+
+def test_diagonal_hadamard_factorises_on_gpu(qw):
+    """H (x) H on the diagonal lattice from a product start: P(x, y) = P1(-x) P1(-y)
+    with P1 the Hadamard walk on the cycle (exact factorisation of the walk)."""
+    L, T = 256, 100
+    a = (0.6, 0.8j)
+    b = (1 / np.sqrt(2), -1 / np.sqrt(2))
+    psi = np.zeros((4, L, L), dtype=complex)
+    for j in range(2):
+        for k in range(2):
+            psi[2 * j + k, 0, 0] = a[j] * b[k]
+    w = qw.Walk((L, L), prec="f64", shift=qw.SHIFT_DIAGONAL).set_coin(inputs.hadamard2()).set_state(psi)
+    w.step(T)
+    P, _ = w.probabilities()
+    Px, _ = oracle.probabilities(oracle.evolve(inputs.localized_1d(L, 0, a), inputs.hadamard(), T))
+    Py, _ = oracle.probabilities(oracle.evolve(inputs.localized_1d(L, 0, b), inputs.hadamard(), T))
+    neg = (-np.arange(L)) % L
+    assert np.abs(P - np.outer(Py[neg], Px[neg])).max() < 1e-13
+    w.close()

@@ -356,3 +356,37 @@ def test_planted_mistakes_are_caught(name, tmp_path, monkeypatch):
         except AssertionError:
             failures += 1
     assert failures > 0, f"mutation {name} passed every pin"
+
+
+# ------------------------------------------------------------ diagonal lattice
+def test_diagonal_lattice_factorises_for_hadamard_coins():
+    """H (x) H on the diagonal lattice: qubit j drives x, qubit k drives y, so a
+    product start stays a product of two 1D Hadamard walks (each mirrored: coin 0
+    moves +1 here, -1 on the cycle):  P(x, y) = P1(-x) P1(-y)."""
+    L, T = 41, 17
+    a = (0.6, 0.8j)
+    b = (1 / np.sqrt(2), -1 / np.sqrt(2))
+    psi = np.zeros((4, L, L), dtype=complex)
+    for j in range(2):
+        for k in range(2):
+            psi[2 * j + k, 0, 0] = a[j] * b[k]
+    P, _ = oracle.probabilities(oracle.evolve(psi, inputs.hadamard2(), T, shift=2))
+    Px, _ = oracle.probabilities(oracle.evolve(inputs.localized_1d(L, 0, a), inputs.hadamard(), T))
+    Py, _ = oracle.probabilities(oracle.evolve(inputs.localized_1d(L, 0, b), inputs.hadamard(), T))
+    neg = (-np.arange(L)) % L
+    assert np.abs(P - np.outer(Py[neg], Px[neg])).max() < 1e-14
+
+
+@pytest.mark.parametrize("coin", ["fourier", "grover", "random"])
+def test_diagonal_lattice_fourier_and_dense(coin):
+    rng = np.random.default_rng(91)
+    C = {"fourier": inputs.fourier(), "grover": inputs.grover(),
+         "random": inputs.random_unitary(4, rng)}[coin]
+    psi0 = inputs.random_state((4, 6, 9), seed=92)
+    want = fourier.evolve_fourier(psi0, C, 13, diagonal=True)
+    got = oracle.evolve(psi0, C, 13, shift=2)
+    assert np.abs(got - want).max() < 1e-12
+    U = dense.diagonal_shift_matrix((9, 6)) @ dense.coin_matrix(C, 54, 4)
+    assert np.abs(dense.apply_power(U, psi0, 5) - oracle.evolve(psi0, C, 5, shift=2)).max() < 1e-12
+    assert np.abs(dense.apply_power(U.conj().T, psi0, 5) -
+                  oracle.evolve(psi0, C, 5, shift=2, adjoint=True)).max() < 1e-12
