@@ -459,6 +459,58 @@ def run_gpu(args, rank, world, local):
     }
 
 
+def run_case(args):
+    """Small named workloads for kernel captures (ncu) and quick timings; prints
+    one JSON line with the case's own time.  Not the benchmark line."""
+    import torch
+    import paper_1003_3779_gb300.qw as qw
+    from paper_1003_3779_gb300 import inputs as _in
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    out = {"case": args.case}
+    if args.case == "torus":
+        L = args.n_sites
+        g = torch.Generator(device="cuda").manual_seed(2)
+        z = torch.randn((4, L, L), dtype=torch.complex64, device="cuda", generator=g)
+        z /= z.abs().pow(2).sum().sqrt()
+        w = qw.Walk((L, L), prec="f32").set_coin(_in.grover()).set_state(z)
+        k = int(args.plan.split(",")[0]) if args.plan else 8
+        w.set_plan(k)
+        w.step(2 * k)
+        a, b = ev(), ev()
+        a.record(stream)
+        w.step(8 * k)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out.update(L=L, k=k, kernel=w.describe()["path"], ms_per_step=a.elapsed_time(b) / (8 * k))
+        w.close()
+    elif args.case == "batch":
+        N, T, th, x0 = _in.batch_1d_params(nwalks=args.walks)
+        coins = np.stack([_in.su2(t) for t in th])
+        b_ = qw.Batch(N, T, coins, x0, _in.BATCH_COIN_STATE).set_plan(int(args.plan.split(",")[0]) if args.plan else 64)
+        b_.step()
+        a, b = ev(), ev()
+        a.record(stream)
+        b_.step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        out.update(walks=args.walks, ms=a.elapsed_time(b))
+        b_.close()
+    elif args.case == "grad":
+        L, T, K = args.n_sites, 64, 64
+        w = qw.Walk((L, L), prec="f32")
+        w.set_coin_phases(_in.grover(), _in.region_grad_phases(L).reshape(-1, 4).astype(np.float32))
+        w.set_state(_in.localized_2d(L))
+        grad = torch.empty((L * L, 4), dtype=torch.float64, device="cuda")
+        rect = _in.region_rect(L, centre=(L // 4, L // 4), size=max(4, L // 16))
+        qw.qw_backward(w.h, rect, T, K, grad)
+        t0 = time.perf_counter()
+        loss = qw.qw_backward(w.h, rect, T, K, grad)
+        out.update(L=L, T=T, K=K, ms=1e3 * (time.perf_counter() - t0), loss=loss)
+        w.close()
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -470,10 +522,16 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--n-sites", type=int, default=N_SITES,
                     help="cycle length (default 2^27; smaller only for profiling captures)")
+    ap.add_argument("--case", default="", choices=["", "torus", "batch", "grad"],
+                    help="run a small named workload for kernel captures instead of the benchmark")
+    ap.add_argument("--walks", type=int, default=4096, help="walks of the batch case")
     ap.add_argument("--plan", default="",
                     help="fixed 'k,tile[,variant]' instead of the autotuner (variant 1 = sweep, the default; 0 = tiles)")
     args = ap.parse_args()
     rank, world, local = dist_env()
+    if args.case:
+        run_case(args)
+        return
 
     if args.impl == "reference":
         if rank != 0:
