@@ -68,8 +68,11 @@ k_step2d_tb(View in, View out, int64_t nx, int64_t ny, int64_t W, int64_t nstrip
 
     // psi_0 of the next row is loaded one iteration ahead, so its latency hides
     // behind the KT levels of the current row
+    // rows stay within one period of the torus (H <= ny, KT < ny is not needed:
+    // q is at most one period outside [0, ny)), so a conditional add wraps them
+    auto wrap_row = [&](int64_t q) { return q < 0 ? q + ny * ((-q + ny - 1) / ny) : (q >= ny ? q % ny : q); };
     auto load_row = [&](int64_t q, C (&a)[4][R]) {
-        const int64_t row = wrap_index(q, ny) * nx;
+        const int64_t row = wrap_row(q) * nx;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             if (vec) {
@@ -140,7 +143,7 @@ k_step2d_tb(View in, View out, int64_t nx, int64_t ny, int64_t W, int64_t nstrip
         // psi_KT of row q - KT: store the columns whose light cone stayed inside the strip
         const int64_t r = q - KT;
         if (r >= y0) {
-            const int64_t orow = wrap_index(r, ny) * nx;
+            const int64_t orow = wrap_row(r) * nx;
             if (j0 >= KT && j0 + R <= KT + wthis && vec) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {

@@ -188,6 +188,7 @@ static void apply_global_coin(qw_walk *w, const double *h) {
     const double alpha = std::sqrt(fro / d);
     w->coin_alpha = std::fabs(alpha - 1.0) <= 1e-5 ? alpha : 1.0;
     w->gain_fb = 1.0;
+    w->drift_pending = 1.0;
 
     // Hadamard class on the cycle with the moving shift: C = lambda * M, M in
     // {+-1}^{2x2}, M = diag(a, c) H diag(1, s) (needs m11 = -m10 m01 m00).
@@ -227,25 +228,31 @@ static double feedback_gain(qw_walk *w, double ideal, bool update = true) {
     return applied;
 }
 
-// Per-step norm-drift factor for the 2D and generic kernels.
-static double drift_gain(qw_walk *w, int steps, bool update = true) {
+// Norm-drift compensation of a rounded coin.  Each launch of K steps scales
+// the norm by alpha^K; the ideal correction alpha^-K is accumulated here and
+// applied in the last launch of a qw_step call (or as soon as it exceeds
+// 2^-16).  Applying factors within a few ulps of 1 at every launch would itself
+// be biased: round-to-nearest of x * (1 - 2^-24) is always x - ulp(x).
+static double take_drift(qw_walk *w, int steps, bool last) {
     if (w->kind == CK_PERSITE || w->kind == CK_PHASE || w->coin_alpha == 1.0) return 1.0;
-    return feedback_gain(w, std::pow(w->coin_alpha, -(double)steps), update);
+    w->drift_pending *= std::pow(w->coin_alpha, -(double)steps);
+    if (!last && std::fabs(w->drift_pending - 1.0) < 1.0 / 65536) return 1.0;
+    const double applied = rounds_to_float(w) ? (double)(float)w->drift_pending : w->drift_pending;
+    w->drift_pending /= applied;
+    return applied;
 }
 
-// Per-step factor that one launch applies `steps` times (the 2D streaming
-// kernel), chosen with the same error feedback as feedback_gain.
-static double drift_gain_per_step(qw_walk *w, int steps) {
-    if (w->kind == CK_PERSITE || w->kind == CK_PHASE || w->coin_alpha == 1.0) return 1.0;
-    const double ideal = 1.0 / w->coin_alpha;
-    const double want = ideal * std::pow(w->gain_fb, -1.0 / steps);
-    const double g = rounds_to_float(w) ? (double)(float)want : want;
-    w->gain_fb *= std::pow(g / ideal, (double)steps);
-    return g;
+// Per-step factor for the 2D and generic kernels: drift_gain(w, 1, last).
+static double drift_gain(qw_walk *w, int steps, bool last = true) { return take_drift(w, steps, last); }
+
+// The per-step factor that a launch applies `steps` times (2D streaming kernel).
+static double drift_gain_per_step(qw_walk *w, int steps, bool last) {
+    const double total = take_drift(w, steps, last);
+    return total == 1.0 ? 1.0 : std::pow(total, 1.0 / steps);
 }
 
 // Pre / post per-plane factors of one 1D launch of K steps.
-static void launch_gains_1d(qw_walk *w, int K, int adj, Step1DArgs &a, bool update = true) {
+static void launch_gains_1d(qw_walk *w, int K, int adj, Step1DArgs &a, bool update = true, bool last = true) {
     if (w->kind == CK_SIGN_P || w->kind == CK_SIGN_M) {
         const double mag = feedback_gain(w, std::pow(w->sign_lambda, (double)K), update);
         const double ak1 = ((K - 1) % 2 == 0 || w->sign_a > 0) ? 1.0 : -1.0;   // a^{K-1}
@@ -258,7 +265,7 @@ static void launch_gains_1d(qw_walk *w, int K, int adj, Step1DArgs &a, bool upda
         }
         return;
     }
-    const double g = drift_gain(w, K, update);
+    const double g = update ? take_drift(w, K, last) : 1.0;
     a.pre0 = a.pre1 = 1.0;
     a.post0 = a.post1 = g;
 }
@@ -291,7 +298,7 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
         a.links = w->has_links ? w->links_dev : nullptr; a.adjoint = adj;
         if (w->kind == CK_SIGN_P || w->kind == CK_SIGN_M) a.kind = CK_COMPLEX;   // generic reads the matrix
         for (int64_t t = 0; t < T; ++t) {
-            a.gain = drift_gain(w, 1);
+            a.gain = drift_gain(w, 1, t + 1 == T);
             a.in = cur_view(w); a.out = next_view(w);
             if ((e = stepgen(w->prec, a, cp, w->stream)) != cudaSuccess) return cuda_error(w, e, "generic step launch");
             w->cur ^= 1;
@@ -310,7 +317,7 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
             // the last, shorter launch of a sweep plan falls back to the tile kernel if needed
             a.variant = (variant == 1 && sweep_ok(w, a.K)) ? 1 : 0;
             if (a.variant == 0) a.K = std::min(a.K, 8 * teff);
-            launch_gains_1d(w, a.K, adj, a);
+            launch_gains_1d(w, a.K, adj, a, true, rem - a.K == 0);
             a.in = cur_view(w); a.out = next_view(w);
             if ((e = step1d(w->prec, a, cp, adj, w->stream)) != cudaSuccess) return cuda_error(w, e, "1D step launch");
             w->cur ^= 1;
@@ -328,7 +335,7 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
         Step2DArgs b = a;
         b.K = K2;
         while (T >= K2) {
-            b.gain = drift_gain_per_step(w, K2);   // applied at each of the K2 steps (1 for Grover / H(x)H)
+            b.gain = drift_gain_per_step(w, K2, T - K2 == 0);   // applied at each of the K2 steps
             b.in = cur_view(w); b.out = next_view(w);
             if ((e = launch_step2d_tb(b, cp, w->stream)) != cudaSuccess) return cuda_error(w, e, "2D blocked step launch");
             w->cur ^= 1;
@@ -336,7 +343,7 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
         }
     }
     for (int64_t t = 0; t < T; ++t) {
-        a.gain = drift_gain(w, 1);
+        a.gain = drift_gain(w, 1, t + 1 == T);
         a.in = cur_view(w); a.out = next_view(w);
         if ((e = step2d(w->prec, a, cp, adj, w->stream)) != cudaSuccess) return cuda_error(w, e, "2D step launch");
         w->cur ^= 1;
@@ -543,6 +550,7 @@ qw_status qw_set_state(qw_walk *w, const void *amp, qw_cdtype dtype, int on_devi
     cudaError_t e = cudaSuccess;
     const View dst = cur_view(w);
     w->gain_fb = 1.0;
+    w->drift_pending = 1.0;
     if (direct_layout(w, dtype)) {
         e = cudaMemcpy2DAsync(w->buf[w->cur], (size_t)w->pitch * w->slot_bytes, amp, plane, plane, w->d,
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, w->stream);

@@ -36,7 +36,14 @@ k_backward2d(View lam_in, View psi_in, View lam_out, View psi_out, int64_t nx, i
     using C = Cx<real>;
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nx * ny) return;
-    const int64_t x = v % nx, y = v / nx;
+    int64_t x, y;
+    if (nx * ny < (int64_t(1) << 31)) {   // 32-bit division where it fits (uniform branch)
+        x = (int)v % (int)nx;
+        y = (int)v / (int)nx;
+    } else {
+        x = v % nx;
+        y = v / nx;
+    }
     const int64_t xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
     const int64_t yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
     // S^dagger: field_c(v) <- field_{src c}(v + e_c); e_0 = +x, e_1 = -x, e_2 = +y, e_3 = -y
@@ -77,8 +84,10 @@ k_backward2d(View lam_in, View psi_in, View lam_out, View psi_out, int64_t nx, i
     double g[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        // -2 Im(conj(a) b), evaluated in double
-        g[k] = -2.0 * ((double)a[k].re * (double)b[k].im - (double)a[k].im * (double)b[k].re);
+        // -2 Im(conj(a) b) in the compute precision (double arithmetic is slow on
+        // this part); only the accumulation over the steps is double
+        const real im = a[k].re * b[k].im - a[k].im * b[k].re;
+        g[k] = -2.0 * (double)im;
         C e;
         expi<real>(pk[k], e);
         S::st(lam_out, k, v, conjmul(e, a[k]));

@@ -41,7 +41,11 @@ struct WalkDesc {
     int64_t pitch;   // sites per plane, a multiple of 64
     int64_t poff;    // first index of the walk in the concatenated probabilities
     float c[8];      // coin, row-major complex (re, im)
-    double alpha;    // sqrt(|C_f|_F^2 / 2) of the float-rounded coin (norm-drift factor per step)
+    // norm-drift compensation of the float-rounded coin (alpha = sqrt(|C_f|_F^2 / 2)):
+    // the last round applies alpha^-T (g_last), the others g_main = 1; computed on
+    // the host, so the kernel does no double arithmetic per round
+    float g_main, g_last;
+    double alpha;
 };
 
 struct BatchArgs {
@@ -108,7 +112,6 @@ k_batch(BatchArgs a) {
         CoinP<float> cp;
 #pragma unroll
         for (int e = 0; e < 4; ++e) { cp.re[e] = d.c[2 * e]; cp.im[e] = d.c[2 * e + 1]; }
-        double fb = 1.0;   // error feedback of the per-round drift factor
         int cur = 0;
         for (int64_t t0 = 0; t0 < d.T;) {
             // while the cone is narrower than the cycle, short rounds clip it more tightly
@@ -118,9 +121,7 @@ k_batch(BatchArgs a) {
             const int64_t ntiles = (d.n + W - 1) / W;
             const int64_t r = t0 + k;
             const bool all = 2 * r + 1 >= d.n;
-            const double ideal = pow(d.alpha, -(double)k);
-            const float g = (float)(ideal / fb);
-            fb *= (double)g / ideal;
+            const float g = (t0 + k >= d.T) ? d.g_last : d.g_main;
             for (int64_t tile = wid; tile < ntiles; tile += nw) {
                 const int64_t o0 = tile * W, o1 = min(o0 + W, d.n);
                 if (!all && !meets_cone(o0, o1, d.x0, r, d.n)) continue;
@@ -211,6 +212,17 @@ static cudaError_t batch_launch(qw_batch *b, cudaStream_t s) {
         else k_batch<P_F32, CK_COMPLEX><<<b->grid, BATCH_THREADS, 0, s>>>(a);
     }
     return cudaGetLastError();
+}
+
+// Per-walk drift factors (see WalkDesc): the whole correction alpha^-T is
+// applied once, in the walk's last round.  Factors within a few ulps of 1,
+// applied every round, would be biased by round-to-nearest.
+static void set_gains(qw_batch *b, int K) {
+    (void)K;
+    for (auto &d : b->walks) {
+        d.g_main = 1.f;
+        d.g_last = (d.T <= 0 || d.alpha == 1.0) ? 1.f : (float)std::pow(d.alpha, -(double)d.T);
+    }
 }
 
 static void drop_graph(qw_batch *b) {
@@ -305,6 +317,7 @@ qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T, const 
     if (e == cudaSuccess) e = dev_alloc((void **)&b->norms_dev, sizeof(double) * nwalks);
     if (e == cudaSuccess) e = dev_alloc((void **)&b->counter, sizeof(int));
     if (e == cudaSuccess) e = dev_alloc((void **)&b->final_dev, sizeof(int) * nwalks);
+    set_gains(b, b->K);
     if (e == cudaSuccess) e = cudaMemcpy(b->walks_dev, b->walks.data(), sizeof(WalkDesc) * nwalks, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->order_dev, b->order.data(), sizeof(int) * nwalks, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
@@ -345,6 +358,9 @@ qw_status qw_batch_set_plan(qw_batch *b, int depth_k) {
         cudaStreamSynchronize(b->stream);
         drop_graph(b);   // the captured launch carries k
         b->K = depth_k;
+        set_gains(b, depth_k);
+        cudaError_t e = cudaMemcpy(b->walks_dev, b->walks.data(), sizeof(WalkDesc) * b->nwalks, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return batch_cuda(b, e, "batch plan");
     }
     return QW_OK;
 }

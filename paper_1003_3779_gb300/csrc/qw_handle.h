@@ -29,6 +29,8 @@ struct qw_walk {
     int sign_a = 1, sign_c = 1, sign_s = 1, sign_sigma = 1;
     // error feedback of the rounded per-launch gains: product of applied / ideal
     double gain_fb = 1.0;
+    // norm-drift factor of the rounded coin not yet applied to the state
+    double drift_pending = 1.0;
     alignas(16) unsigned char coinp[512];  // CoinP<real> in compute precision
     void *coins_dev = nullptr;             // per-site matrices (compute precision)
     size_t coins_bytes = 0;
