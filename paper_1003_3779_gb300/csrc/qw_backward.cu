@@ -9,7 +9,9 @@
 //     dL/dphi_{v,k} = sum_t 2 Re( conj(a_t(v)_k) i b_t(v)_k ) = sum_t -2 Im(conj(a_k) b_k),
 //     a_t = B^dagger S^dagger lambda_{t+1},   b_t = D_v psi_t = B^dagger S^dagger psi_{t+1}.
 // So one backward step pulls both lambda_{t+1} and psi_{t+1} through S^dagger,
-// applies B^dagger to both, accumulates the gradient in double, and emits
+// applies B^dagger to both, adds the gradient term to a per-segment
+// accumulator in the compute precision (flushed into the double gradient at the
+// end of every segment of K steps), and emits
 // lambda_t = D^dagger a and psi_t = D^dagger b.  psi_t is rebuilt from psi_{t+1}
 // (the walk is unitary) instead of stored; it is re-seeded from a forward
 // checkpoint every K steps, which bounds the drift of the reconstruction to K
@@ -30,7 +32,7 @@ template <> __device__ __forceinline__ void expi<double>(float a, Cx<double> &e)
 template <int P, int FF, int GROVER>
 __global__ void __launch_bounds__(256)
 k_backward2d(View lam_in, View psi_in, View lam_out, View psi_out, int64_t nx, int64_t ny,
-             CoinP<typename St<P>::real> cp, const float *__restrict__ phi, double *__restrict__ grad) {
+             CoinP<typename St<P>::real> cp, const float *__restrict__ phi, typename St<P>::real *__restrict__ gseg) {
     using real = typename St<P>::real;
     using S = St<P>;
     using C = Cx<real>;
@@ -81,23 +83,29 @@ k_backward2d(View lam_in, View psi_in, View lam_out, View psi_out, int64_t nx, i
     }
     const float4 ph = reinterpret_cast<const float4 *>(phi)[v];
     const float pk[4] = {ph.x, ph.y, ph.z, ph.w};
-    double g[4];
+    real g[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        // -2 Im(conj(a) b) in the compute precision (double arithmetic is slow on
-        // this part); only the accumulation over the steps is double
-        const real im = a[k].re * b[k].im - a[k].im * b[k].re;
-        g[k] = -2.0 * (double)im;
+        // -2 Im(conj(a) b) in the compute precision; the segment's running sum
+        // stays in that precision and is added into the double gradient once per
+        // segment of K steps (double arithmetic is slow on this part)
+        g[k] = (a[k].im * b[k].re - a[k].re * b[k].im) * (real)2;
         C e;
         expi<real>(pk[k], e);
         S::st(lam_out, k, v, conjmul(e, a[k]));
         S::st(psi_out, k, v, conjmul(e, b[k]));
     }
-    double2 *gp = reinterpret_cast<double2 *>(grad + 4 * v);
-    double2 g01 = gp[0], g23 = gp[1];
-    g01.x += g[0]; g01.y += g[1]; g23.x += g[2]; g23.y += g[3];
-    gp[0] = g01;
-    gp[1] = g23;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) gseg[4 * v + k] += g[k];
+}
+
+// grad += gseg (double), gseg = 0: the end of one segment of the adjoint sweep.
+template <class R>
+__global__ void k_flush_segment(R *__restrict__ gseg, double *__restrict__ grad, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    grad[i] += (double)gseg[i];
+    gseg[i] = (R)0;
 }
 
 // lambda_T = 1_R psi_T, and per-block partial sums of |psi_T|^2 over R.
@@ -141,7 +149,8 @@ __global__ void k_sum_blocks(const double *partials, int n, double *out) {
 
 template <int P>
 static cudaError_t backward_step(const qw_walk *w, View lam_in, View psi_in, View lam_out, View psi_out,
-                                 double *grad) {
+                                 void *gseg_v) {
+    auto *gseg = static_cast<typename St<P>::real *>(gseg_v);
     const auto &cp = *reinterpret_cast<const CoinP<typename St<P>::real> *>(w->coinp);
     const unsigned blocks = (unsigned)((w->ns + 255) / 256);
     bool grover = true;
@@ -150,7 +159,7 @@ static cudaError_t backward_step(const qw_walk *w, View lam_in, View psi_in, Vie
             grover = grover && w->coin_host[2 * (4 * r + c)] == (r == c ? -0.5 : 0.5) &&
                      w->coin_host[2 * (4 * r + c) + 1] == 0.0;
     const bool ff = w->shift == QW_SHIFT_FLIPFLOP;
-#define QW_BWD(FFV, GV) k_backward2d<P, FFV, GV><<<blocks, 256, 0, w->stream>>>(lam_in, psi_in, lam_out, psi_out, w->nx, w->ny, cp, w->phi_dev, grad)
+#define QW_BWD(FFV, GV) k_backward2d<P, FFV, GV><<<blocks, 256, 0, w->stream>>>(lam_in, psi_in, lam_out, psi_out, w->nx, w->ny, cp, w->phi_dev, gseg)
     if (ff) { if (grover) QW_BWD(1, 1); else QW_BWD(1, 0); }
     else { if (grover) QW_BWD(0, 1); else QW_BWD(0, 0); }
 #undef QW_BWD
@@ -175,7 +184,8 @@ extern "C" qw_status qw_backward(qw_walk *w, const int64_t rect[4], int64_t T, i
     const int64_t nseg = (T + K - 1) / K;
     const size_t sb = w->state_bytes;
     const size_t gbytes = sizeof(double) * 4 * (size_t)w->ns;
-    const size_t need = (size_t)(nseg + 1) * sb + 2 * sb + (on_device ? 0 : gbytes);
+    const size_t segbytes = (w->prec == QW_F32 ? 4 : 8) * 4 * (size_t)w->ns;   // per-segment accumulator
+    const size_t need = (size_t)(nseg + 1) * sb + 2 * sb + (on_device ? 0 : gbytes) + segbytes + 256;
     cudaError_t e;
     if (w->grad_scratch_bytes < need) {
         cudaStreamSynchronize(w->stream);
@@ -189,6 +199,7 @@ extern "C" qw_status qw_backward(qw_walk *w, const int64_t rect[4], int64_t T, i
     auto ckpt = [&](int64_t s) { return View{base + s * sb, w->pitch, w->d}; };
     View lam[2] = {View{base + (nseg + 1) * sb, w->pitch, w->d}, View{base + (nseg + 2) * sb, w->pitch, w->d}};
     double *grad = on_device ? grad_phi : reinterpret_cast<double *>(base + (nseg + 3) * sb);
+    void *gseg = base + (nseg + 3) * sb + (on_device ? 0 : gbytes);
 
     // forward with a checkpoint every K steps
     e = cudaMemcpyAsync(ckpt(0).p, w->buf[w->cur], sb, cudaMemcpyDeviceToDevice, w->stream);
@@ -209,6 +220,7 @@ extern "C" qw_status qw_backward(qw_walk *w, const int64_t rect[4], int64_t T, i
     k_sum_blocks<<<1, 32, 0, w->stream>>>(w->partials, nb, w->norm_dev);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(w, e, "region seed");
     if ((e = cudaMemsetAsync(grad, 0, gbytes, w->stream)) != cudaSuccess) return cuda_error(w, e, "gradient clear");
+    if ((e = cudaMemsetAsync(gseg, 0, segbytes, w->stream)) != cudaSuccess) return cuda_error(w, e, "gradient clear");
 
     // backward, segment by segment, psi re-seeded from the checkpoint at each boundary
     int li = 0;
@@ -218,13 +230,18 @@ extern "C" qw_status qw_backward(qw_walk *w, const int64_t rect[4], int64_t T, i
         int pi = 0;
         for (int64_t t = t_hi - 1; t >= t_lo; --t) {
             View psi_out = view_of(w, pi);
-            e = w->prec == QW_F32 ? backward_step<P_F32>(w, lam[li], psi_in, lam[li ^ 1], psi_out, grad)
-                                  : backward_step<P_F64>(w, lam[li], psi_in, lam[li ^ 1], psi_out, grad);
+            e = w->prec == QW_F32 ? backward_step<P_F32>(w, lam[li], psi_in, lam[li ^ 1], psi_out, gseg)
+                                  : backward_step<P_F64>(w, lam[li], psi_in, lam[li ^ 1], psi_out, gseg);
             if (e != cudaSuccess) return cuda_error(w, e, "backward step");
             li ^= 1;
             psi_in = psi_out;
             pi ^= 1;
         }
+        const int64_t n4 = 4 * w->ns;
+        const unsigned fb = (unsigned)((n4 + 255) / 256);
+        if (w->prec == QW_F32) k_flush_segment<float><<<fb, 256, 0, w->stream>>>(static_cast<float *>(gseg), grad, n4);
+        else k_flush_segment<double><<<fb, 256, 0, w->stream>>>(static_cast<double *>(gseg), grad, n4);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(w, e, "segment flush");
     }
 
     // leave the walk at psi_T; hand out the gradient and the loss
