@@ -416,6 +416,11 @@ k_step1d_sweep(View in, View out, int64_t n, int K, int nch, int64_t nseg, CoinP
         cp_async_commit();
     };
 
+    // the warm-up chunk (j = -1) reads its left edge from the parity-0 edge
+    // buffer: zero it once, so the level loop needs no special case
+    for (int i = lane; i < 2 * K; i += 32) edge[i] = czero<real>();
+    __syncwarp();
+
     C a0[R], a1[R];
     prefetch(-1);
     for (int j = -1; j < nchs; ++j) {
@@ -443,7 +448,7 @@ k_step1d_sweep(View in, View out, int64_t n, int K, int nch, int64_t nseg, CoinP
         // Two levels per loop iteration ping-pong between a and b, so results
         // always go to registers that hold nothing live (no moves at all).
         auto level = [&](int t, const C (&s0)[R], const C (&s1)[R], C (&d0)[R], C (&d1)[R]) {
-            const C h2 = j >= 0 ? ein[2 * t] : czero<real>(), h1 = j >= 0 ? ein[2 * t + 1] : czero<real>();
+            const C h2 = ein[2 * t], h1 = ein[2 * t + 1];   // zeros for the warm-up chunk
             if (!ADJ) {
                 C top2, top1;   // coin-1 results of the two highest sites: they leave the lane
 #pragma unroll
