@@ -179,14 +179,15 @@ def cpu_oracle_sample(target_s=12.0):
 # ------------------------------------------------------------------ GPU arm
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("k_step1d.cuh", "qw_internal.cuh"):   # the device code of every 1D step kernel
+    for f in ("k_step1d.cuh", "qw_internal.cuh", "launch_step.cuh"):   # 1D step kernels and their launch
         h.update(open(os.path.join(ROOT, "paper_1003_3779_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel="k_step1d_sweep"):
+def ncu_traffic(kernel="k_step1d_sweep", tile=None):
     """DRAM bytes per launch of the 1D step kernel from the committed ncu summary,
-    or None when the summary is missing or was taken on different kernel sources."""
+    or None when the summary is missing, was taken on different kernel sources,
+    or on another tile (sites per lane) than the one the benchmark runs."""
     p = os.path.join(ROOT, "profiles", f"{kernel}_su2_f32.md")
     try:
         s = open(p).read()
@@ -194,7 +195,10 @@ def ncu_traffic(kernel="k_step1d_sweep"):
         return None
     m = re.search(r"kernel_hash:\s*([0-9a-f]+)", s)
     b = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", s)
+    t = re.search(r"sites_per_lane:\s*(\d+)", s)
     if not m or not b or m.group(1) != kernel_hash():
+        return None
+    if tile is not None and (not t or int(t.group(1)) != tile):
         return None
     return float(b.group(1))
 
@@ -225,7 +229,7 @@ def run_gpu(args, rank, world, local):
         tune = {"tuned": False, "plan": args.plan}
     else:
         tune = json.loads(w.autotune())
-    K, tile = w.plan()
+    K, tile, _variant = w.plan_ex()
     desc = w.describe()
     launches_step = math.ceil(T_STEPS / K)
 
@@ -275,7 +279,7 @@ def run_gpu(args, rank, world, local):
     ach_tflops = flops_launch / avg_launch_s / 1e12
     ach_gbs = bytes_launch / avg_launch_s / 1e9
     alu_frac, hbm_frac = ach_tflops / alu_peak, ach_gbs / hbm_gbs
-    traffic = ncu_traffic(desc["path"])
+    traffic = ncu_traffic(desc["path"], tile)
     if alu_frac >= hbm_frac:
         roof = {"bound": "alu", "achieved": ach_tflops, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": alu_frac, "traffic": traffic,
@@ -287,8 +291,7 @@ def run_gpu(args, rank, world, local):
         roof = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm_gbs, "unit": "GB/s",
                 "frac": hbm_frac, "traffic": traffic, "peak_source": f"{peak_src} HBM copy",
                 "alu_view": {"achieved_tflops": ach_tflops, "peak_tflops": alu_peak, "frac": alu_frac}}
-    roof.update({"kernel": "%s<f32,R=%d,%s coin>" % (desc["path"], 16 if desc["path"] == "k_step1d_sweep" else tile,
-                                                     desc["coin_kind"]), "k": K,
+    roof.update({"kernel": "%s<f32,R=%d,%s coin>" % (desc["path"], tile, desc["coin_kind"]), "k": K,
                  "flops_per_site_step": flops_site_step,
                  "avg_launch_ms": avg_launch_s * 1e3,
                  "effective_bytes_per_site_step": bytes_launch / N_SITES / k_eff})

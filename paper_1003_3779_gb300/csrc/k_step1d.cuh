@@ -364,12 +364,38 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Lane 31 stores (v2, v1) at eout and loads (v2, v1) from ein; the other lanes
+// keep their values.  Predicated shared accesses: no branch, no select.
+// Float pairs are one 16-byte access each way (both addresses 16-byte aligned).
+__device__ __forceinline__ void edge_swap31(int lane, unsigned eout, unsigned ein, Cx<float> &v2, Cx<float> &v1) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %4, 31;\n\t"
+                 "@p st.shared.v4.f32 [%5], {%0, %1, %2, %3};\n\t"
+                 "@p ld.shared.v4.f32 {%0, %1, %2, %3}, [%6];\n\t}"
+                 : "+f"(v2.re), "+f"(v2.im), "+f"(v1.re), "+f"(v1.im)
+                 : "r"(lane), "r"(eout), "r"(ein)
+                 : "memory");
+}
+__device__ __forceinline__ void edge_swap31(int lane, unsigned eout, unsigned ein, Cx<double> &v2, Cx<double> &v1) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %4, 31;\n\t"
+                 "@p st.shared.v2.f64 [%5], {%0, %1};\n\t"
+                 "@p st.shared.v2.f64 [%5+16], {%2, %3};\n\t"
+                 "@p ld.shared.v2.f64 {%0, %1}, [%6];\n\t"
+                 "@p ld.shared.v2.f64 {%2, %3}, [%6+16];\n\t}"
+                 : "+d"(v2.re), "+d"(v2.im), "+d"(v1.re), "+d"(v1.im)
+                 : "r"(lane), "r"(eout), "r"(ein)
+                 : "memory");
+}
+
 // Position of a lane's c-th 16-byte unit in the chunk buffer: the XOR keeps the
 // eight lanes that share a shared-memory wavefront on distinct bank groups.
 template <int CPL>
 __device__ __forceinline__ int swz(int lane, int c) {
-    constexpr int G = 8 / CPL;
-    return lane * CPL + (c ^ ((lane / G) & (CPL - 1)));
+    if constexpr (CPL >= 8) {
+        return lane * CPL + (c ^ (lane & 7));
+    } else {
+        constexpr int G = 8 / CPL;
+        return lane * CPL + (c ^ ((lane / G) & (CPL - 1)));
+    }
 }
 
 template <int P, int R>
@@ -417,7 +443,8 @@ k_step1d_sweep(View in, View out, int64_t n, int K, int nch, int64_t nseg, CoinP
     };
 
     // the warm-up chunk (j = -1) reads its left edge from the parity-0 edge
-    // buffer: zero it once, so the level loop needs no special case
+    // buffer: zero it once, so the level loop needs no special case.  After
+    // this, lane 31 alone writes and reads the edge entries.
     for (int i = lane; i < 2 * K; i += 32) edge[i] = czero<real>();
     __syncwarp();
 
@@ -442,13 +469,20 @@ k_step1d_sweep(View in, View out, int64_t n, int K, int nch, int64_t nseg, CoinP
             for (int i = 0; i < R; ++i) a1[i] = rmul(pre1, a1[i]);
         }
         const int par = j & 1;
-        const C *ein = edge + (size_t)(par ^ 1) * K * 2;   // handed over by the previous chunk
-        C *eout = edge + (size_t)par * K * 2;
+        const int from = (lane + 31) & 31;   // the lane below, lane 31 for lane 0
+        // shared addresses of the edge entries handed over by the previous chunk
+        // (ein) and to the next one (eout)
+        const unsigned si = (unsigned)__cvta_generic_to_shared(edge + (size_t)(par ^ 1) * K * 2);
+        const unsigned so = (unsigned)__cvta_generic_to_shared(edge + (size_t)par * K * 2);
         // One level of the sliding frame, from (s0, s1) into fresh arrays (d0, d1).
         // Two levels per loop iteration ping-pong between a and b, so results
         // always go to registers that hold nothing live (no moves at all).
+        // The two values that leave a lane at its top go to the lane above by a
+        // rotating shuffle; lane 31's pair instead goes to the next chunk through
+        // eout, and lane 31 sends on, in its place, the pair the previous chunk
+        // left in ein (zeros for the warm-up chunk), which the rotation delivers
+        // to lane 0.  Predicated shared accesses of lane 31, no selects.
         auto level = [&](int t, const C (&s0)[R], const C (&s1)[R], C (&d0)[R], C (&d1)[R]) {
-            const C h2 = ein[2 * t], h1 = ein[2 * t + 1];   // zeros for the warm-up chunk
             if (!ADJ) {
                 C top2, top1;   // coin-1 results of the two highest sites: they leave the lane
 #pragma unroll
@@ -461,22 +495,17 @@ k_step1d_sweep(View in, View out, int64_t n, int K, int nch, int64_t nseg, CoinP
                     if (i + 2 < R) { if (!FF) d1[i + 2] = n1; else d0[i + 2] = n1; }
                     else if (i == R - 1) top1 = n1;
                     else top2 = n1;
+                    if (i == R - 2)   // both leave-values ready: lane 31 swaps in ein's
+                        edge_swap31(lane, so + t * 2 * (unsigned)sizeof(C), si + t * 2 * (unsigned)sizeof(C), top2, top1);
                 }
-                C lm2 = shfl_up(top2, 1), lm1 = shfl_up(top1, 1);
-                // edge hand-over without divergence: every lane reads the broadcast
-                // value, lane 0 selects it; lane 31's store is a predicated store
-                lm2 = lane == 0 ? h2 : lm2;
-                lm1 = lane == 0 ? h1 : lm1;
-                if (lane == 31) { eout[2 * t] = top2; eout[2 * t + 1] = top1; }
+                const C lm2 = shfl_idx(top2, from), lm1 = shfl_idx(top1, from);
                 if (!FF) { d1[0] = lm2; d1[1] = lm1; } else { d0[0] = lm2; d0[1] = lm1; }
             } else {
                 // S^dagger in the sliding frame: moving b1 = a1 (same index), b0 = a0 two down;
                 // flip-flop b1 = a0, b0 = a1 two down.  Then C^dagger at the site.
-                const C e2 = FF ? s1[R - 2] : s0[R - 2], e1 = FF ? s1[R - 1] : s0[R - 1];
-                C lm2 = shfl_up(e2, 1), lm1 = shfl_up(e1, 1);
-                lm2 = lane == 0 ? h2 : lm2;
-                lm1 = lane == 0 ? h1 : lm1;
-                if (lane == 31) { eout[2 * t] = e2; eout[2 * t + 1] = e1; }
+                C e2 = FF ? s1[R - 2] : s0[R - 2], e1 = FF ? s1[R - 1] : s0[R - 1];
+                edge_swap31(lane, so + t * 2 * (unsigned)sizeof(C), si + t * 2 * (unsigned)sizeof(C), e2, e1);
+                const C lm2 = shfl_idx(e2, from), lm1 = shfl_idx(e1, from);
 #pragma unroll
                 for (int i = R - 1; i >= 0; --i) {
                     const C b0 = i >= 2 ? (FF ? s1[i - 2] : s0[i - 2]) : (i == 0 ? lm2 : lm1);
@@ -486,18 +515,30 @@ k_step1d_sweep(View in, View out, int64_t n, int K, int nch, int64_t nseg, CoinP
             }
         };
         C b0[R], b1[R];
+        // blocks of levels; the Hadamard class rescales after each full block of
+        // SIGN_RESCALE_STEPS (its unnormalised additions grow by sqrt(2) per step)
+        constexpr bool SIGN = CK == CK_SIGN_P || CK == CK_SIGN_M;
+        const int blk = SIGN ? SIGN_RESCALE_STEPS : K;
         int t = 0;
 #pragma unroll 1
-        for (; t + 1 < K; t += 2) {
-            level(t, a0, a1, b0, b1);
-            level(t + 1, b0, b1, a0, a1);
+        for (int tb = 0; tb + 1 < K; tb += blk) {
+            const int te = min(tb + blk, K);
+#pragma unroll 1
+            for (t = tb; t + 1 < te; t += 2) {
+                level(t, a0, a1, b0, b1);
+                level(t + 1, b0, b1, a0, a1);
+            }
+            if (SIGN && t == tb + SIGN_RESCALE_STEPS) {   // 2^-SIGN_RESCALE_LOG2, exact
+                const real sc = (real)(1.0 / (double)(1ull << SIGN_RESCALE_LOG2));
+#pragma unroll
+                for (int i = 0; i < R; ++i) { a0[i] = rmul(sc, a0[i]); a1[i] = rmul(sc, a1[i]); }
+            }
         }
         if (t < K) {
             level(t, a0, a1, b0, b1);
 #pragma unroll
             for (int i = 0; i < R; ++i) { a0[i] = b0[i]; a1[i] = b1[i]; }
         }
-        __syncwarp();   // this chunk's edges are visible to lane 0 of the next one
         if (j >= 0) {
             if (!is_one(post0)) {
 #pragma unroll

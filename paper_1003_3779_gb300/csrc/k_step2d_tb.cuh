@@ -101,7 +101,7 @@ k_step2d_tb(View in, View out, int64_t nx, int64_t ny, int64_t W, int64_t nstrip
                 C ai[4] = {a[0][i], a[1][i], a[2][i], a[3][i]}, pi[4];
                 coin4g<CK, real>(cp, ai, pi);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) N[i][c] = gain_one ? pi[c] : rmul(gain, pi[c]);
+                for (int c = 0; c < 4; ++c) N[i][c] = pi[c];
             }
         }
         // levels 1..KT: level s produces psi_s of row q - s
@@ -136,13 +136,19 @@ k_step2d_tb(View in, View out, int64_t nx, int64_t ny, int64_t W, int64_t nstrip
                     C pi[4];
                     coin4g<CK, real>(cp, psi[i], pi);
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) N[i][c] = gain_one ? pi[c] : rmul(gain, pi[c]);
+                    for (int c = 0; c < 4; ++c) N[i][c] = pi[c];
                 }
             }
         }
         // psi_KT of row q - KT: store the columns whose light cone stayed inside the strip
         const int64_t r = q - KT;
         if (r >= y0) {
+            if (!gain_one) {   // the launch's drift correction, once per KT steps
+#pragma unroll
+                for (int i = 0; i < R; ++i)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) psi[i][c] = rmul(gain, psi[i][c]);
+            }
             const int64_t orow = wrap_row(r) * nx;
             if (j0 >= KT && j0 + R <= KT + wthis && vec) {
 #pragma unroll

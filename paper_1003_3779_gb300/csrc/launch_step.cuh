@@ -79,15 +79,29 @@ static bool go1d_kind(const Step1DArgs &a, const CoinP<typename St<P>::real> &cp
     }
 }
 
-// Sites per lane of the sweep kernel (one 16-byte unit count per lane that is a
-// power of two between 2 and 8); the double-float form has no sweep kernel.
-template <int P> struct SweepR { static constexpr int R = 16; };
-template <> struct SweepR<P_F64> { static constexpr int R = 8; };
+// Sites per lane compiled for the sweep kernel (R * SLOT_BYTES / 16 = 2..16
+// sixteen-byte units per lane and plane); the double-float form has none.
+// The larger tile halves the per-level overhead (edge hand-over, shuffles)
+// per site and allows deeper k; the smaller one takes cycles that are a
+// multiple of half its chunk.
+template <int P> struct SweepTiles { static constexpr int A = 16, B = 32; };
+template <> struct SweepTiles<P_F64> { static constexpr int A = 8, B = 8; };
+template <> struct SweepTiles<P_COMP> { static constexpr int A = 0, B = 0; };
 
-template <int P, int CK, int FF, int ADJ>
+// The sites per lane a sweep plan with this tile runs on a cycle of n sites:
+// the requested tile if it is compiled, else the larger tile when n is a
+// multiple of its chunk, else the smaller one.
+template <int P>
+int sweep_tile(int64_t n, int tile) {
+    using T = SweepTiles<P>;
+    if (T::A == 0) return 0;
+    if (tile == T::A || tile == T::B) return tile;
+    return n % (32LL * T::B) == 0 ? T::B : T::A;
+}
+
+template <int P, int R, int CK, int FF, int ADJ>
 static cudaError_t go1d_sweep(const Step1DArgs &a, const CoinP<typename St<P>::real> &cp, cudaStream_t s) {
     using real = typename St<P>::real;
-    constexpr int R = SweepR<P>::R;
     using SW = Sweep<P, R>;
     constexpr int warps = 4;
     const size_t smem = warps * SW::warp_bytes(a.K);
@@ -115,24 +129,25 @@ static cudaError_t go1d_sweep(const Step1DArgs &a, const CoinP<typename St<P>::r
     return cudaGetLastError();
 }
 
-template <int P, int ADJ>
+template <int P, int R, int ADJ>
 static cudaError_t go1d_sweep_kind(const Step1DArgs &a, const CoinP<typename St<P>::real> &cp, cudaStream_t s) {
     const bool ff = a.shift == QW_SHIFT_FLIPFLOP;
     switch (a.kind) {
-        case CK_REAL: return ff ? go1d_sweep<P, CK_REAL, 1, ADJ>(a, cp, s) : go1d_sweep<P, CK_REAL, 0, ADJ>(a, cp, s);
-        case CK_COMPLEX: return ff ? go1d_sweep<P, CK_COMPLEX, 1, ADJ>(a, cp, s) : go1d_sweep<P, CK_COMPLEX, 0, ADJ>(a, cp, s);
-        case CK_SIGN_P: return ff ? cudaErrorInvalidValue : go1d_sweep<P, CK_SIGN_P, 0, ADJ>(a, cp, s);
-        case CK_SIGN_M: return ff ? cudaErrorInvalidValue : go1d_sweep<P, CK_SIGN_M, 0, ADJ>(a, cp, s);
+        case CK_REAL: return ff ? go1d_sweep<P, R, CK_REAL, 1, ADJ>(a, cp, s) : go1d_sweep<P, R, CK_REAL, 0, ADJ>(a, cp, s);
+        case CK_COMPLEX: return ff ? go1d_sweep<P, R, CK_COMPLEX, 1, ADJ>(a, cp, s) : go1d_sweep<P, R, CK_COMPLEX, 0, ADJ>(a, cp, s);
+        case CK_SIGN_P: return ff ? cudaErrorInvalidValue : go1d_sweep<P, R, CK_SIGN_P, 0, ADJ>(a, cp, s);
+        case CK_SIGN_M: return ff ? cudaErrorInvalidValue : go1d_sweep<P, R, CK_SIGN_M, 0, ADJ>(a, cp, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-// Can the sweep kernel run this launch?  (n a multiple of the chunk, 2 <= K < chunk / 2.)
+// Can the sweep kernel run this launch?  (n a multiple of the chunk of the
+// tile sweep_tile picks, 2 <= K < chunk / 2.)
 template <int P>
-bool sweep_ok(int64_t n, int K, int kind) {
+bool sweep_ok(int64_t n, int K, int kind, int tile) {
     if (P == P_COMP || kind == CK_PERSITE || kind == CK_PHASE) return false;
-    constexpr int B = Sweep<P, SweepR<P>::R>::B;
-    return n % B == 0 && n >= B && K >= 2 && K <= B / 2 - 1;
+    const int64_t B = 32LL * sweep_tile<P>(n, tile);
+    return B > 0 && n % B == 0 && n >= B && K >= 2 && K <= B / 2 - 1;
 }
 
 // Largest K the 1D kernel accepts for tile R: at least half the tile is output.
@@ -150,15 +165,18 @@ cudaError_t step1d_t(const Step1DArgs &a0, const void *coinp, int adj, cudaStrea
     using T = Tiles1D<P>;
     const auto &cp = *static_cast<const CoinP<typename St<P>::real> *>(coinp);
     Step1DArgs a = a0;
-    a.tile = tile1d_effective<P>(a.tile, a.kind, adj);
     if (a.variant == 1) {   // time-skewed sweep
         if constexpr (P == P_COMP) {
             return cudaErrorInvalidValue;
         } else {
-            if (!sweep_ok<P>(a.n, a.K, a.kind)) return cudaErrorInvalidValue;
-            return adj ? go1d_sweep_kind<P, 1>(a, cp, s) : go1d_sweep_kind<P, 0>(a, cp, s);
+            using ST = SweepTiles<P>;
+            if (!sweep_ok<P>(a.n, a.K, a.kind, a.tile)) return cudaErrorInvalidValue;
+            if (sweep_tile<P>(a.n, a.tile) == ST::B)
+                return adj ? go1d_sweep_kind<P, ST::B, 1>(a, cp, s) : go1d_sweep_kind<P, ST::B, 0>(a, cp, s);
+            return adj ? go1d_sweep_kind<P, ST::A, 1>(a, cp, s) : go1d_sweep_kind<P, ST::A, 0>(a, cp, s);
         }
     }
+    a.tile = tile1d_effective<P>(a.tile, a.kind, adj);
     if (a.K < 1 || a.K > max_k_1d(a.tile)) return cudaErrorInvalidValue;
     const bool ff = a.shift == QW_SHIFT_FLIPFLOP;
     if (a.K == 1) {   // one step per launch: the streaming kernel
@@ -259,5 +277,6 @@ cudaError_t generic_t(const StepGenericArgs &a, const void *coinp, cudaStream_t 
         return generic_t<PREC>(a, cp, s);                                                               \
     }                                                                                                   \
     int tile1d_##SUFFIX(int tile, int kind, int adj) { return tile1d_effective<PREC>(tile, kind, adj); } \
-    bool sweep_ok_##SUFFIX(int64_t n, int K, int kind) { return sweep_ok<PREC>(n, K, kind); }          \
+    bool sweep_ok_##SUFFIX(int64_t n, int K, int kind, int tile) { return sweep_ok<PREC>(n, K, kind, tile); } \
+    int sweep_tile_##SUFFIX(int64_t n, int tile) { return sweep_tile<PREC>(n, tile); }                   \
     }

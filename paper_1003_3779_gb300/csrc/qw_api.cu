@@ -93,16 +93,25 @@ static int tile1d(int prec, int tile, int kind, int adj) {
     }
     return 0;
 }
-static bool sweep_ok(const qw_walk *w, int K) {
+// Sweep plans: `tile` is the sites per lane (0 or an uncompiled value: the
+// launcher's default for this cycle length).
+static bool sweep_ok(const qw_walk *w, int K, int tile) {
     if (w->ndim != 1 || w->bc != QW_BC_PERIODIC || w->has_links) return false;
     switch (w->prec) {
-        case QW_F64: return sweep_ok_f64(w->nx, K, w->kind);
-        case QW_F32: return sweep_ok_f32(w->nx, K, w->kind);
-        case QW_F32_BF16STORE: return sweep_ok_bf16(w->nx, K, w->kind);
+        case QW_F64: return sweep_ok_f64(w->nx, K, w->kind, tile);
+        case QW_F32: return sweep_ok_f32(w->nx, K, w->kind, tile);
+        case QW_F32_BF16STORE: return sweep_ok_bf16(w->nx, K, w->kind, tile);
     }
     return false;
 }
-static int sweep_max_k(const qw_walk *w) { return w->prec == QW_F64 ? 127 : 255; }
+static int sweep_tile(const qw_walk *w, int tile) {
+    switch (w->prec) {
+        case QW_F64: return sweep_tile_f64(w->nx, tile);
+        case QW_F32: return sweep_tile_f32(w->nx, tile);
+        case QW_F32_BF16STORE: return sweep_tile_bf16(w->nx, tile);
+    }
+    return 0;
+}
 
 // tiles compiled for the forward 1D kernel, per precision
 static void tiles_of(int prec, int &a, int &b) {
@@ -122,9 +131,10 @@ static void default_plan(const qw_walk *w, int &k, int &tile, int &variant) {
         case QW_F32_COMP: tile = 4; k = 8; break;
         default: tile = 16; k = 32; break;
     }
-    if (sweep_ok(w, w->prec == QW_F64 ? 8 : 64)) {
+    if (sweep_ok(w, w->prec == QW_F64 ? 8 : 64, 0)) {
         variant = 1;
         k = w->prec == QW_F64 ? 8 : 64;
+        tile = sweep_tile(w, 0);
     }
 }
 
@@ -245,16 +255,13 @@ static double take_drift(qw_walk *w, int steps, bool last) {
 // Per-step factor for the 2D and generic kernels: drift_gain(w, 1, last).
 static double drift_gain(qw_walk *w, int steps, bool last = true) { return take_drift(w, steps, last); }
 
-// The per-step factor that a launch applies `steps` times (2D streaming kernel).
-static double drift_gain_per_step(qw_walk *w, int steps, bool last) {
-    const double total = take_drift(w, steps, last);
-    return total == 1.0 ? 1.0 : std::pow(total, 1.0 / steps);
-}
-
 // Pre / post per-plane factors of one 1D launch of K steps.
 static void launch_gains_1d(qw_walk *w, int K, int adj, Step1DArgs &a, bool update = true, bool last = true) {
     if (w->kind == CK_SIGN_P || w->kind == CK_SIGN_M) {
-        const double mag = feedback_gain(w, std::pow(w->sign_lambda, (double)K), update);
+        // the sweep kernel rescales by 2^-SIGN_RESCALE_LOG2 every SIGN_RESCALE_STEPS steps
+        const int m = a.variant == 1 ? K / SIGN_RESCALE_STEPS : 0;
+        const double mag = feedback_gain(w, std::ldexp(std::pow(w->sign_lambda, (double)K), SIGN_RESCALE_LOG2 * m),
+                                         update);
         const double ak1 = ((K - 1) % 2 == 0 || w->sign_a > 0) ? 1.0 : -1.0;   // a^{K-1}
         if (!adj) {
             a.pre0 = 1.0; a.pre1 = (double)(w->sign_sigma * w->sign_s);
@@ -311,11 +318,12 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
         const int teff = tile1d(w->prec, tile, w->kind, adj);
         if (variant != 1) K = std::min(K, 8 * teff);
         Step1DArgs a{};
-        a.n = w->nx; a.tile = teff; a.shift = w->shift; a.kind = w->kind; a.coins = w->coins_dev;
+        a.n = w->nx; a.shift = w->shift; a.kind = w->kind; a.coins = w->coins_dev;
         for (int64_t rem = T; rem > 0;) {
             a.K = (int)std::min<int64_t>(K, rem);
             // the last, shorter launch of a sweep plan falls back to the tile kernel if needed
-            a.variant = (variant == 1 && sweep_ok(w, a.K)) ? 1 : 0;
+            a.variant = (variant == 1 && sweep_ok(w, a.K, tile)) ? 1 : 0;
+            a.tile = a.variant == 1 ? tile : teff;
             if (a.variant == 0) a.K = std::min(a.K, 8 * teff);
             launch_gains_1d(w, a.K, adj, a, true, rem - a.K == 0);
             a.in = cur_view(w); a.out = next_view(w);
@@ -335,7 +343,7 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
         Step2DArgs b = a;
         b.K = K2;
         while (T >= K2) {
-            b.gain = drift_gain_per_step(w, K2, T - K2 == 0);   // applied at each of the K2 steps
+            b.gain = drift_gain(w, K2, T - K2 == 0);   // applied once, to the launch's output
             b.in = cur_view(w); b.out = next_view(w);
             if ((e = launch_step2d_tb(b, cp, w->stream)) != cudaSuccess) return cuda_error(w, e, "2D blocked step launch");
             w->cur ^= 1;
@@ -690,12 +698,11 @@ qw_status qw_set_plan_ex(qw_walk *w, int depth_k, int tile, int variant) {
         if (st == QW_OK && depth_k == 0) w->plan_variant = -1;
         return st;
     }
-    if (w->ndim != 1 || depth_k < 1 || depth_k > sweep_max_k(w) || !sweep_ok(w, std::max(depth_k, 2)))
+    if (w->ndim != 1 || depth_k < 1 || !sweep_ok(w, std::max(depth_k, 2), tile))
         return set_error(w, QW_EINVAL, "the sweep kernel needs the periodic 1D walk, N a multiple of its "
-                                       "chunk, a global coin, FP32/BF16/FP64 and 1 <= k < chunk / 2");
-    int dk, dt, dv;
-    default_plan(w, dk, dt, dv);
-    w->plan_k = depth_k; w->plan_tile = tile1d(w->prec, tile ? tile : dt, CK_REAL, 0); w->plan_variant = 1;
+                                       "chunk (32 x tile sites), a global coin, FP32/BF16/FP64 and "
+                                       "1 <= k < chunk / 2");
+    w->plan_k = depth_k; w->plan_tile = sweep_tile(w, tile); w->plan_variant = 1;
     w->plan_user = true;
     return QW_OK;
 }
@@ -704,7 +711,7 @@ qw_status qw_get_plan_ex(const qw_walk *w, int *depth_k, int *tile, int *variant
     if (!w || !depth_k || !tile || !variant) return QW_EINVAL;
     int k, t, v;
     effective_plan(w, k, t, v);
-    if (w->ndim == 1) t = tile1d(w->prec, t, w->kind, 0);
+    if (w->ndim == 1) t = v == 1 ? sweep_tile(w, t) : tile1d(w->prec, t, w->kind, 0);
     *depth_k = k; *tile = t; *variant = v;
     return QW_OK;
 }
@@ -715,7 +722,7 @@ qw_status qw_describe(const qw_walk *w, char *buf, size_t len) {
                                   "hadamard_class", "hadamard_class"};
     int k, t, var;
     effective_plan(w, k, t, var);
-    if (w->ndim == 1) t = tile1d(w->prec, t, w->kind, 0);
+    if (w->ndim == 1) t = var == 1 ? sweep_tile(w, t) : tile1d(w->prec, t, w->kind, 0);
     const bool generic = w->bc != QW_BC_PERIODIC || w->has_links ||
                          (w->ndim == 2 && (w->kind == CK_PERSITE ||
                                            (w->kind == CK_PHASE && !(w->prec == QW_F32 || w->prec == QW_F64))));
@@ -883,22 +890,30 @@ extern "C" qw_status qw_autotune(qw_walk *w, char *report, size_t report_len) {
     }
     int best_v = 0;
     if (err == cudaSuccess) {
-        const int sks[] = {8, 16, 24, 32, 48, 64, 96, 128, 160, 192, 255};
-        for (int k : sks) {
-            if (k > sweep_max_k(w) || !sweep_ok(w, k)) continue;
-            a.K = k; a.variant = 1;
-            launch_gains_1d(w, k, 0, a, false);
-            err = step1d(w->prec, a, w->coinp, 0, w->stream);
+        // both sweep tiles (even k: an odd k adds a register copy per chunk)
+        const int sks[] = {8, 16, 24, 32, 48, 64, 96, 128, 160, 192, 224, 254, 288, 320, 384, 448, 510};
+        int last_r = 0;
+        for (int st : {8, 16, 32}) {
+            const int r = sweep_tile(w, st);
+            if (r != st || r == last_r) continue;   // not compiled for this precision
+            last_r = r;
+            for (int k : sks) {
+                if (!sweep_ok(w, k, r)) continue;
+                a.K = k; a.variant = 1; a.tile = r;
+                launch_gains_1d(w, k, 0, a, false);
+                err = step1d(w->prec, a, w->coinp, 0, w->stream);
+                if (err != cudaSuccess) break;
+                cudaEventRecord(e0, w->stream);
+                const int reps = 3;
+                for (int rep = 0; rep < reps; ++rep) step1d(w->prec, a, w->coinp, 0, w->stream);
+                cudaEventRecord(e1, w->stream);
+                if ((err = cudaEventSynchronize(e1)) != cudaSuccess) break;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                const float per_step = ms / (reps * k);
+                if (per_step < best) { best = per_step; best_k = k; best_v = 1; best_t = r; }
+            }
             if (err != cudaSuccess) break;
-            cudaEventRecord(e0, w->stream);
-            const int reps = 3;
-            for (int r = 0; r < reps; ++r) step1d(w->prec, a, w->coinp, 0, w->stream);
-            cudaEventRecord(e1, w->stream);
-            if ((err = cudaEventSynchronize(e1)) != cudaSuccess) break;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            const float per_step = ms / (reps * k);
-            if (per_step < best) { best = per_step; best_k = k; best_v = 1; }
         }
         a.variant = 0;
     }

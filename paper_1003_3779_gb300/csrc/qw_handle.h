@@ -91,9 +91,12 @@ cudaError_t launch_generic_f32(const StepGenericArgs &, const void *, cudaStream
 cudaError_t launch_generic_f64(const StepGenericArgs &, const void *, cudaStream_t);
 cudaError_t launch_generic_bf16(const StepGenericArgs &, const void *, cudaStream_t);
 cudaError_t launch_generic_comp(const StepGenericArgs &, const void *, cudaStream_t);
-bool sweep_ok_f32(int64_t, int, int);
-bool sweep_ok_f64(int64_t, int, int);
-bool sweep_ok_bf16(int64_t, int, int);
+bool sweep_ok_f32(int64_t, int, int, int);
+bool sweep_ok_f64(int64_t, int, int, int);
+bool sweep_ok_bf16(int64_t, int, int, int);
+int sweep_tile_f32(int64_t, int);
+int sweep_tile_f64(int64_t, int);
+int sweep_tile_bf16(int64_t, int);
 int tile1d_f32(int, int, int);
 int tile1d_f64(int, int, int);
 int tile1d_bf16(int, int, int);

@@ -133,6 +133,9 @@ __device__ __forceinline__ double shfl_up(double v, int d) { return __shfl_up_sy
 __device__ __forceinline__ double shfl_down(double v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
 __device__ __forceinline__ ff shfl_up(ff v, int d) { return {shfl_up(v.hi, d), shfl_up(v.lo, d)}; }
 __device__ __forceinline__ ff shfl_down(ff v, int d) { return {shfl_down(v.hi, d), shfl_down(v.lo, d)}; }
+__device__ __forceinline__ float shfl_idx(float v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ double shfl_idx(double v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+template <class R> __device__ __forceinline__ Cx<R> shfl_idx(Cx<R> v, int l) { return {shfl_idx(v.re, l), shfl_idx(v.im, l)}; }
 template <class R> __device__ __forceinline__ Cx<R> shfl_up(Cx<R> v, int d) { return {shfl_up(v.re, d), shfl_up(v.im, d)}; }
 template <class R> __device__ __forceinline__ Cx<R> shfl_down(Cx<R> v, int d) { return {shfl_down(v.re, d), shfl_down(v.im, d)}; }
 
@@ -291,6 +294,15 @@ enum CoinKind {
     CK_SIGN_P = 6,    // sigma = +1: p0 = a0 + a1, p1 = a0 - a1
     CK_SIGN_M = 7     // sigma = -1: p0 = a0 - a1, p1 = a0 + a1
 };
+
+// The Hadamard-class kernels add without the factor lambda = 1/sqrt(2) per
+// step, so amplitudes grow by sqrt(2) per step; float overflows after about
+// 250 steps.  The sweep kernel, which runs up to 511 steps per launch,
+// multiplies the state by 2^-SIGN_RESCALE_LOG2 (exact) after every
+// SIGN_RESCALE_STEPS steps, and the host folds 2^(SIGN_RESCALE_LOG2 * m), m the
+// number of rescales in the launch, into the launch's lambda^K.
+constexpr int SIGN_RESCALE_STEPS = 64;
+constexpr int SIGN_RESCALE_LOG2 = 32;
 
 // One global d x d coin in compute precision, passed by value (kernel
 // parameter space, read through the constant cache).

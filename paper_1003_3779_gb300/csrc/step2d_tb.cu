@@ -45,7 +45,8 @@ bool step2d_tb_ok(int prec, int kind, int K, int shift) {
            (kind == CK_REAL || kind == CK_COMPLEX || kind == CK_GROVER || kind == CK_HH);
 }
 
-// K steps (K = 4 or 8) in one launch; the gain is per step.
+// K steps (K = 4 or 8) in one launch; the gain (drift correction) is applied
+// once, to the launch's output.
 cudaError_t launch_step2d_tb(const Step2DArgs &a, const void *coinp, cudaStream_t s) {
     const auto &cp = *static_cast<const CoinP<float> *>(coinp);
     switch (a.K) {

@@ -247,35 +247,73 @@ def test_norm_drift_compensated_long_run(qw, theta):
     w.close()
 
 
-SWEEP_CASES = [("f32", 512 * 37), ("f32", 512), ("bf16", 512 * 20), ("f64", 256 * 35)]
+# (precision, N, sites per lane): both compiled tiles of the float forms (chunks
+# of 512 and 1024 sites), several segments with a short last one, one-chunk cycles
+SWEEP_CASES = [("f32", 512 * 37, 16), ("f32", 512, 16), ("f32", 1024 * 19, 32), ("f32", 1024, 32),
+               ("bf16", 512 * 21, 16), ("bf16", 1024 * 11, 32), ("f64", 256 * 35, 8)]
+SWEEP_COINS = {"hadamard_class": inputs.su2(np.pi / 4), "real": inputs.su2(0.3),
+               "complex": inputs.su2(0.3, 0.2, -0.5)}
 
 
-@pytest.mark.parametrize("prec,N", SWEEP_CASES)
-@pytest.mark.parametrize("k", [2, 3, 17, 64, 127])
-@pytest.mark.parametrize("coin", ["hadamard_class", "real", "complex"])
-@pytest.mark.parametrize("shift", [0, 1])
-@pytest.mark.parametrize("adj", [False, True])
-def test_sweep_kernel(qw, prec, N, k, coin, shift, adj):
-    """The time-skewed sweep (variant 1) against the oracle: several segments, a
-    short last segment, one-chunk cycles, odd and large depths, all coin classes."""
-    C = {"hadamard_class": inputs.su2(np.pi / 4), "real": inputs.su2(0.3),
-         "complex": inputs.su2(0.3, 0.2, -0.5)}[coin]
+def _sweep_against_oracle(qw, prec, N, tile, k, coin, shift, adj):
+    C = SWEEP_COINS[coin]
     T = 3 * k + 5
     psi0 = inputs.random_state((2, N), seed=17)
     want = oracle.evolve(psi0, C, T, shift=shift, adjoint=adj)
     w = qw.Walk((N,), prec=prec, shift=shift).set_coin(C)
-    w.set_plan_ex(k, 0, 1)
-    assert w.plan_ex()[2] == 1 and w.describe()["path"] == "k_step1d_sweep"
+    w.set_plan_ex(k, tile, 1)
+    assert w.plan_ex() == (k, tile, 1) and w.describe()["path"] == "k_step1d_sweep"
     w.set_state(psi0)
     (w.step_adjoint if adj else w.step)(T)
     assert maxabs(w.state(), want) < amp_tol(prec, T, k)
     w.close()
 
 
+@pytest.mark.parametrize("prec,N,tile", SWEEP_CASES)
+@pytest.mark.parametrize("k", [2, 3, 17, 64, 127])
+@pytest.mark.parametrize("coin", list(SWEEP_COINS))
+@pytest.mark.parametrize("shift", [0, 1])
+@pytest.mark.parametrize("adj", [False, True])
+def test_sweep_kernel(qw, prec, N, tile, k, coin, shift, adj):
+    """The time-skewed sweep (variant 1) against the oracle: several segments, a
+    short last segment, one-chunk cycles, odd and large depths, all coin classes."""
+    _sweep_against_oracle(qw, prec, N, tile, k, coin, shift, adj)
+
+
+@pytest.mark.parametrize("prec,N,tile", [c for c in SWEEP_CASES if c[2] >= 16])
+@pytest.mark.parametrize("k", [160, 255, 256, 400, 511])
+@pytest.mark.parametrize("coin", ["hadamard_class", "complex"])
+@pytest.mark.parametrize("adj", [False, True])
+def test_sweep_kernel_deep(qw, prec, N, tile, k, coin, adj):
+    """Depths up to the largest each tile takes (k < chunk / 2): the warm-up
+    chunk's error front and the edge buffer at their limits."""
+    if k > 16 * tile - 1:
+        pytest.skip("deeper than this tile takes")
+    _sweep_against_oracle(qw, prec, N, tile, k, coin, 0, adj)
+
+
+def test_sweep_default_tile_follows_the_cycle_length(qw):
+    for N, tile in ((1024 * 5, 32), (512 * 5, 16)):
+        w = qw.Walk((N,), prec="f32").set_coin(inputs.hadamard())
+        w.set_plan_ex(64, 0, 1)
+        assert w.plan_ex() == (64, tile, 1)
+        w.close()
+
+
 def test_sweep_rejected_where_it_cannot_run(qw):
     w = qw.Walk((1000,), prec="f32").set_coin(inputs.hadamard())
     with pytest.raises(qw.QWError):
         w.set_plan_ex(16, 0, 1)          # 1000 is not a multiple of 512
+    w.close()
+    w = qw.Walk((512 * 3,), prec="f32").set_coin(inputs.hadamard())
+    with pytest.raises(qw.QWError):
+        w.set_plan_ex(16, 32, 1)         # 1536 is not a multiple of the 1024-site chunk
+    with pytest.raises(qw.QWError):
+        w.set_plan_ex(256, 16, 1)        # k must stay below half the 512-site chunk
+    w.close()
+    w = qw.Walk((1024 * 3,), prec="f32").set_coin(inputs.hadamard())
+    with pytest.raises(qw.QWError):
+        w.set_plan_ex(512, 32, 1)        # k must stay below half the 1024-site chunk
     w.close()
     w = qw.Walk((1024,), prec="comp").set_coin(inputs.hadamard())
     with pytest.raises(qw.QWError):
