@@ -298,7 +298,7 @@ def run_gpu(args, rank, world, local):
 
     # k = 1 (one step per HBM round trip): the plain fused step against the HBM roof
     plan_saved = w.plan_ex()
-    w.set_plan(1, tile)
+    w.set_plan(1, 0)
     qw.qw_set_state(w.h, dev0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     qw.qw_step(w.h, 8)
@@ -404,7 +404,7 @@ def run_gpu(args, rank, world, local):
             wf.set_coin(C)
             wf.set_state(dev0)
             wf.autotune()
-            Kf, tf = wf.plan()
+            Kf, tf, _ = wf.plan_ex()
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)

@@ -3,7 +3,7 @@
 // Each walk is the 1D walk of Sec. 2.2 (cycle Z_N, coin dim 2, U = S (I (x) C)
 // of Sec. 2.1) with its own N, T and 2x2 coin, started localised at x0.  One
 // CTA owns one walk at a time: it pops the next walk from a global counter
-// (walks sorted by N*T, longest first), zeroes the walk's two state buffers,
+// (walks sorted by light-cone work, largest first), zeroes the walk's two state buffers,
 // places the initial amplitude, and advances the walk k steps per round with
 // the same warp register-tile kernel as the single cycle (tb_tile), its four
 // warps sharing the tiles of the walk and meeting at a __syncthreads between
@@ -295,9 +295,14 @@ qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T, const 
     b->total_sites = poff;
     b->order.resize(nwalks);
     std::iota(b->order.begin(), b->order.end(), 0);
-    std::stable_sort(b->order.begin(), b->order.end(), [&](int p, int q) {
-        return (double)N[p] * (double)T[p] > (double)N[q] * (double)T[q];
-    });
+    // longest first by light-cone work, sum_{t<T} min(N, 2t+1) site-steps (the
+    // tiles a walk actually computes), not by N*T
+    auto work = [&](int i) {
+        const double n = (double)N[i], t = (double)T[i];
+        const double tc = std::min(t, std::ceil((n - 1) / 2));   // steps before the cone covers the cycle
+        return tc * tc + (t - tc) * n;
+    };
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int p, int q) { return work(p) > work(q); });
     const int slot = prec == QW_F32_BF16STORE ? 4 : 8;
     b->buf_bytes = (size_t)base * slot;
 
