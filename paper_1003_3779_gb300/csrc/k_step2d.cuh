@@ -62,11 +62,12 @@ template <int CK, class R>
 __device__ __forceinline__ void coin4(const CoinP<R> &cp, const Cx<R> *__restrict__ m, const SiteCoin<R> &sc,
                                       const Cx<R> (&a)[4], Cx<R> (&p)[4]) {
     if (CK == CK_GROVER) {
-        // G = (1/2) J - I: off-diagonal entries are the 1/2 (cp.re[1])
+        // G = (1/2) J - I: off-diagonal entries are the 1/2 (cp.re[1]).  p_r =
+        // s/2 - a_r as one fused multiply-add: s/2 is exact, so this rounds
+        // exactly as the separate multiply and subtraction would.
         Cx<R> s = cadd(cadd(a[0], a[1]), cadd(a[2], a[3]));
-        Cx<R> half = rmul(cp.re[1], s);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) p[r] = csub(half, a[r]);
+        for (int r = 0; r < 4; ++r) p[r] = rfma(cp.re[1], s, Cx<R>{-a[r].re, -a[r].im});
     } else if (CK == CK_HH) {
         Cx<R> u0 = cadd(a[0], a[1]), u1 = csub(a[0], a[1]);
         Cx<R> u2 = cadd(a[2], a[3]), u3 = csub(a[2], a[3]);

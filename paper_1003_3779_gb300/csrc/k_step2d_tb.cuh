@@ -23,11 +23,22 @@
 
 namespace qw {
 
-// Site-free coin for the streaming kernel (global coins only).
+// Site-free coin for the streaming kernel (global coins only).  H (x) H is
+// applied without its factor 1/2 (the butterflies only, exact in binary
+// scaling): the kernel multiplies the output by 2^-KT once, exactly.
 template <int CK, class R>
 __device__ __forceinline__ void coin4g(const CoinP<R> &cp, const Cx<R> (&a)[4], Cx<R> (&p)[4]) {
-    SiteCoin<R> sc;
-    coin4<CK, R>(cp, (const Cx<R> *)nullptr, sc, a, p);
+    if constexpr (CK == CK_HH) {
+        const Cx<R> u0 = cadd(a[0], a[1]), u1 = csub(a[0], a[1]);
+        const Cx<R> u2 = cadd(a[2], a[3]), u3 = csub(a[2], a[3]);
+        p[0] = cadd(u0, u2);
+        p[1] = cadd(u1, u3);
+        p[2] = csub(u0, u2);
+        p[3] = csub(u1, u3);
+    } else {
+        SiteCoin<R> sc;
+        coin4<CK, R>(cp, (const Cx<R> *)nullptr, sc, a, p);
+    }
 }
 
 template <int P, int KT, int CK, int FF>
@@ -64,6 +75,7 @@ k_step2d_tb(View in, View out, int64_t nx, int64_t ny, int64_t W, int64_t nstrip
 #pragma unroll
             for (int c = 0; c < 3; ++c) A[s][i][c] = czero<real>();
         }
+    if constexpr (CK == CK_HH) gain = gain * (real)(1.0 / (double)(1u << KT));   // the factors 1/2 of H (x) H
     const bool gain_one = is_one(gain);
 
     // psi_0 of the next row is loaded one iteration ahead, so its latency hides
