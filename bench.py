@@ -361,9 +361,17 @@ def run_gpu(args, rank, world, local):
             torch.cuda.synchronize()
             tb = a.elapsed_time(b) / 1e3 / 3
             _, nb_ = bt.probabilities()
+            # the real 2x2 coin is 8 FP32 instructions (4 FMUL, 4 FFMA) per site-step;
+            # against the FP32 issue rate over the light-cone (active) site-steps only
+            inst_rate = 8.0 * (active / 2.0) / tb / 1e12
+            issue_peak = SMS * FP32_LANES * sm_max_mhz * 1e6 / 1e12
             batch[pname] = {"dense_site_coin_updates_per_s": dense / tb,
                             "active_site_coin_updates_per_s": active / tb, "ms_per_batch": tb * 1e3,
-                            "k": tune_b["k"], "max_norm_err": float(np.abs(nb_ - 1).max())}
+                            "k": tune_b["k"], "variant": tune_b.get("variant"), "cta_walks": tune_b.get("cta_walks"),
+                            "alu_view": {"achieved_tinst_per_s": inst_rate, "peak_tinst_per_s": issue_peak,
+                                         "frac": inst_rate / issue_peak,
+                                         "note": "8 FP32 instructions per active site-step (real coin)"},
+                            "max_norm_err": float(np.abs(nb_ - 1).max())}
             bt.close()
 
     # region-mass gradient on the 1024^2 torus (forward with checkpoints + adjoint sweep)

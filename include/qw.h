@@ -232,9 +232,9 @@ qw_status qw_probabilities_noalloc(const void *amp, qw_cdtype dtype, int coin_di
  * (state storage; arithmetic is float), anything else QW_EUNSUPPORTED.  All
  * arrays are host pointers; QW_EINVAL for N < 1, T < 0 or x0 outside [0, N).
  * Device memory: two state buffers for all walks (ping-pong), their
- * probabilities (float) and norms.  One CTA advances one walk at a time; a
- * walk's tiles outside the light cone [x0 - t, x0 + t] of its localised start
- * are skipped (exact zeros). */
+ * probabilities (float) and norms.  The default kernel (variant 1 of
+ * qw_batch_set_plan_ex) sweeps each walk's light cone [x0 - t, x0 + t] only;
+ * the state outside it stays exactly zero. */
 qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T,
                           const double *coins, const int64_t *x0,
                           const double *coin_state, qw_precision prec,
@@ -246,13 +246,35 @@ qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T,
  * from the initial states. */
 qw_status qw_batch_step(qw_batch *b);
 
-/* Temporal depth k (steps per round, 1..128) of the batched kernel; the tile
- * is fixed at 16 sites per lane.  Changing k re-captures the graph. */
+/* Temporal depth k (steps per round, 1..128; default 96) of the batched
+ * kernel; the tile is fixed at 16 sites per lane.  Changing k re-captures the
+ * graph. */
 qw_status qw_batch_set_plan(qw_batch *b, int depth_k);
 qw_status qw_batch_get_plan(const qw_batch *b, int *depth_k, int *tile);
 
-/* Time the batch for k in {8, ..., 128} (each timing runs the whole batch from
- * its initial states) and keep the fastest; report as for qw_autotune. */
+/* The same with the kernel variant: 0 = warp register tiles, each
+ * recomputing a halo of k sites on both sides, tiles outside the light cone
+ * skipped; 1 = time-skewed window sweep (the sweep of qw_set_plan_ex variant 1
+ * over the chunks that cover a walk's light cone, no halo; over the whole
+ * cycle with warm-up chunks once the cone nearly covers it).  Both give the
+ * same results up to rounding order.  QW_EINVAL for another variant. */
+qw_status qw_batch_set_plan_ex(qw_batch *b, int depth_k, int variant);
+qw_status qw_batch_get_plan_ex(const qw_batch *b, int *depth_k, int *tile, int *variant);
+
+/* Work split of variant 1: a walk whose light-cone work sum_{t<T} min(N, 2t+1)
+ * (site-steps) is at least `split` times the batch's mean work per resident warp
+ * is shared by the four warps of a CTA (segments with warm-up chunks, a
+ * barrier between passes); every other walk is swept by one warp alone.  0
+ * puts every walk on a CTA; a huge value (the default, 1e30) every walk on a
+ * warp.  Results do not depend on it.  QW_EINVAL for a negative or NaN value;
+ * re-captures the graph.  qw_batch_cta_walks: how many walks run on a CTA
+ * (-1 for a null handle). */
+qw_status qw_batch_set_split(qw_batch *b, double split);
+int qw_batch_cta_walks(const qw_batch *b);
+
+/* Time the batch for k in {8, ..., 128} and both variants (each timing runs
+ * the whole batch from its initial states) and keep the fastest; report as
+ * for qw_autotune. */
 qw_status qw_batch_autotune(qw_batch *b, char *report, size_t report_len);
 
 /* Probabilities of all walks, concatenated in walk order (walk i starts at

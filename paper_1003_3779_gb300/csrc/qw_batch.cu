@@ -55,8 +55,9 @@ struct BatchArgs {
     void *buf0, *buf1;
     float *P;
     double *norms;
-    int *counter;
+    int *counter;    // [0]: next walk (variant 0; variant 1: next big walk), [1]: next small walk
     int *final_buf;
+    int nbig;        // variant 1: walks order[0, nbig) run on a whole CTA, the rest on single warps
     int K;           // steps per round once the light cone covers the cycle
     int Ks;          // steps per round while it does not (finer cone clipping)
     float cs[4];     // coin state at x0: (re, im) of coin 0 and coin 1
@@ -73,6 +74,143 @@ __device__ __forceinline__ bool meets_cone(int64_t a, int64_t b, int64_t x0, int
     return a < hi && b > lo;
 }
 
+// ---------------------------------------------------------------- window sweep
+// The time-skewed sweep of k_step1d_sweep, over a window of one walk's cycle:
+// frame chunks j of B = 32R sites start at site L + jB (mod n); after K levels
+// chunk j holds sites L + jB - K + [0, B), which it writes out.  The walk only
+// depends on its left in the frame, so a chunk needs from the chunk before it
+// the two values per level that lane 31 hands over through the edge buffer.
+// Chunks [j0, j1) of one segment are swept in order by one warp.  The first
+// chunk's left edge is either zero (warm = false: the state is zero left of
+// the window, outside the light cone) or comes from a warm-up chunk j0 - 1
+// recomputed from a zero edge (its error front moves two sites per level, so
+// K < B/2 - 1 leaves its right edge exact).  Chunks that are not a contiguous,
+// 16-byte aligned run of the cycle (across site n-1 -> 0, or after it when n is
+// odd) are fetched site by site.
+__device__ __forceinline__ void cp_async_bytes8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_bytes4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+template <int P, int CK>
+__device__ __forceinline__ void window_segment(View in, View out, int64_t n, int K, int64_t L, int j0, int j1,
+                                            bool warm, CoinP<float> cp, float post, unsigned char *wbase,
+                                            int lane) {
+    using S = St<P>;
+    using C = Cx<float>;
+    constexpr int R = BATCH_R;
+    using SW = Sweep<P, R>;
+    constexpr int B = SW::B, CPL = SW::CPL, VEC = S::VEC, UPV = 16 / S::SLOT_BYTES;
+    uint4 *cbuf = reinterpret_cast<uint4 *>(wbase);
+    C *edge = reinterpret_cast<C *>(wbase + SW::chunk_bytes);
+    const int jfirst = warm ? j0 - 1 : j0;
+    {   // the first chunk reads its left edge from parity (jfirst & 1) ^ 1
+        C *e0 = edge + (size_t)((jfirst & 1) ^ 1) * K * 2;
+        for (int i = lane; i < 2 * K; i += 32) e0[i] = C{0.f, 0.f};
+    }
+    __syncwarp();
+    auto site = [&](int64_t x) { const int64_t r = x % n; return r < 0 ? r + n : r; };
+    auto prefetch = [&](int j) {
+        const int64_t start = site(L + (int64_t)j * B);
+        if (start + B <= n && start % VEC == 0) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const char *g = static_cast<const char *>(in.p) + (c * in.pitch + start) * S::SLOT_BYTES;
+#pragma unroll
+                for (int i = 0; i < CPL; ++i) {
+                    const int u = i * 32 + lane;
+                    cp_async16(cbuf + c * 32 * CPL + swz<CPL>(u / CPL, u % CPL), g + (size_t)u * 16);
+                }
+            }
+        } else {
+            // this lane's own R sites, one slot at a time, wrapping around the cycle
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const int64_t g = site(start + (int64_t)lane * R + i);
+                    unsigned char *dst = reinterpret_cast<unsigned char *>(cbuf + c * 32 * CPL + swz<CPL>(lane, i / UPV)) +
+                                         (i % UPV) * S::SLOT_BYTES;
+                    const char *src = static_cast<const char *>(in.p) + (c * in.pitch + g) * S::SLOT_BYTES;
+                    if constexpr (S::SLOT_BYTES == 8) cp_async_bytes8(dst, src);
+                    else cp_async_bytes4(dst, src);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+
+    C a0[R], a1[R];
+    prefetch(jfirst);
+    const int from = (lane + 31) & 31;
+    for (int j = jfirst; j < j1; ++j) {
+        cp_async_wait_all();
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < CPL; ++u) {
+            S::unpack(cbuf[swz<CPL>(lane, u)], &a0[u * VEC]);
+            S::unpack(cbuf[32 * CPL + swz<CPL>(lane, u)], &a1[u * VEC]);
+        }
+        __syncwarp();
+        if (j + 1 < j1) prefetch(j + 1);
+        const int par = j & 1;
+        const unsigned si = (unsigned)__cvta_generic_to_shared(edge + (size_t)(par ^ 1) * K * 2);
+        const unsigned so = (unsigned)__cvta_generic_to_shared(edge + (size_t)par * K * 2);
+        // one level of the moving walk in the sliding frame (see k_step1d_sweep)
+        auto level = [&](int t, const C (&s0)[R], const C (&s1)[R], C (&d0)[R], C (&d1)[R]) {
+            C top2, top1;
+#pragma unroll
+            for (int i = R - 1; i >= 0; --i) {
+                C n0, n1;
+                coin2<CK>(cp, (const C *)nullptr, s0[i], s1[i], n0, n1);
+                d0[i] = n0;
+                if (i + 2 < R) d1[i + 2] = n1;
+                else if (i == R - 1) top1 = n1;
+                else top2 = n1;
+                if (i == R - 2) edge_swap31(lane, so + t * 2 * (unsigned)sizeof(C), si + t * 2 * (unsigned)sizeof(C), top2, top1);
+            }
+            d1[0] = shfl_idx(top2, from);
+            d1[1] = shfl_idx(top1, from);
+        };
+        C b0[R], b1[R];
+        int t = 0;
+#pragma unroll 1
+        for (; t + 1 < K; t += 2) {
+            level(t, a0, a1, b0, b1);
+            level(t + 1, b0, b1, a0, a1);
+        }
+        if (t < K) {
+            level(t, a0, a1, b0, b1);
+#pragma unroll
+            for (int i = 0; i < R; ++i) { a0[i] = b0[i]; a1[i] = b1[i]; }
+        }
+        if (j >= j0) {
+            if (post != 1.f) {
+#pragma unroll
+                for (int i = 0; i < R; ++i) { a0[i] = rmul(post, a0[i]); a1[i] = rmul(post, a1[i]); }
+            }
+            const int64_t g0 = site(L + (int64_t)j * B - K + (int64_t)lane * R);
+            if (g0 + R <= n && g0 % VEC == 0) {
+#pragma unroll
+                for (int i = 0; i < R; i += VEC) { S::stv(out, 0, g0 + i, &a0[i]); S::stv(out, 1, g0 + i, &a1[i]); }
+            } else {
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const int64_t g = site(g0 + i);
+                    S::st(out, 0, g, a0[i]);
+                    S::st(out, 1, g, a1[i]);
+                }
+            }
+        }
+    }
+}
+
+// Variant 0: one CTA per walk, warp register tiles with a halo of k sites
+// (tb_tile), tiles outside the light cone skipped.
 template <int P, int CK>
 __global__ void __launch_bounds__(BATCH_THREADS)
 k_batch(BatchArgs a) {
@@ -155,6 +293,126 @@ k_batch(BatchArgs a) {
     }
 }
 
+
+// Variant 1: the window sweep.  A walk is advanced in passes of k steps; a
+// pass sweeps the chunks that cover the light cone (frame from the cone's left
+// end, whose left is zero), or the whole cycle with a warm-up chunk once the
+// cone, widened by the margins, reaches round it.  The largest walks
+// (order[0, nbig)) are each shared by the four warps of a CTA, which split the
+// chunks of a pass into segments (each after the first with a warm-up chunk)
+// and meet at a barrier between passes; every other walk is swept by a single
+// warp alone, with no warm-up chunks and no barrier.  Results are the same
+// bits either way.
+template <int P, int CK>
+__device__ __forceinline__ void run_walk_sweep(const BatchArgs &a, int w, bool cta, int g, int gs, int wid, int nw,
+                                               double *s_red, unsigned char *wbase) {
+    using S = St<P>;
+    constexpr int R = BATCH_R, B = 32 * R, VEC = S::VEC;
+    const int lane = threadIdx.x & 31;
+    auto sync = [cta] { if (cta) __syncthreads(); else __syncwarp(); };
+    const WalkDesc d = a.walks[w];
+    View in{static_cast<char *>(a.buf0) + d.base * S::SLOT_BYTES, d.pitch, 2};
+    View out{static_cast<char *>(a.buf1) + d.base * S::SLOT_BYTES, d.pitch, 2};
+    {
+        const int64_t nvec = 2 * d.pitch * S::SLOT_BYTES / 16;
+        uint4 z = make_uint4(0, 0, 0, 0);
+        for (int64_t i = g; i < nvec; i += gs) {
+            reinterpret_cast<uint4 *>(in.p)[i] = z;
+            reinterpret_cast<uint4 *>(out.p)[i] = z;
+        }
+    }
+    sync();
+    if (g == 0) {
+        S::st(in, 0, d.x0, Cx<float>{a.cs[0], a.cs[1]});
+        S::st(in, 1, d.x0, Cx<float>{a.cs[2], a.cs[3]});
+    }
+    sync();
+    CoinP<float> cp;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) { cp.re[e] = d.c[2 * e]; cp.im[e] = d.c[2 * e + 1]; }
+    int cur = 0;
+    for (int64_t t0 = 0; t0 < d.T;) {
+        const int k = (int)min((int64_t)a.K, d.T - t0);
+        // window: from the cone's left end at t0 (rounded down to the vector
+        // width) far enough that the outputs, shifted left by k, cover the
+        // cone's right end at t0 + k
+        int64_t L = d.x0 - t0;
+        L -= ((L % VEC) + VEC) % VEC;
+        const int64_t span = d.x0 + t0 + 2 * k + 1 - L;
+        const bool win = span + 2 * k + B <= d.n;   // the zero run left of L is outside the cone, not its far side
+        int nch;
+        if (win) {
+            nch = (int)((span + B - 1) / B);
+        } else {
+            L = 0;
+            nch = (int)((d.n + B - 1) / B);
+        }
+        // on a CTA, segments of at least two chunks, at most one per warp
+        const int nseg = max(1, min(nw, nch / 2));
+        const float gl = (t0 + k >= d.T) ? d.g_last : d.g_main;
+        if (wid < nseg) {
+            const int j0 = (int)((int64_t)nch * wid / nseg), j1 = (int)((int64_t)nch * (wid + 1) / nseg);
+            window_segment<P, CK>(in, out, d.n, k, L, j0, j1, !win || wid > 0, cp, gl, wbase, lane);
+        }
+        sync();
+        View tv = in; in = out; out = tv;
+        cur ^= 1;
+        t0 += k;
+    }
+    double acc = 0.0;
+    for (int64_t x = g; x < d.n; x += gs) {
+        const Cx<float> u = S::ld(in, 0, x), v = S::ld(in, 1, x);
+        const float p = __fmaf_rn(u.re, u.re, __fmaf_rn(u.im, u.im, __fmaf_rn(v.re, v.re, v.im * v.im)));
+        a.P[d.poff + x] = p;
+        acc += (double)p;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (cta) {
+        if (lane == 0) s_red[wid] = acc;
+        __syncthreads();
+        if (g == 0) {
+            double tot = 0.0;
+            for (int i = 0; i < nw; ++i) tot += s_red[i];
+            a.norms[w] = tot;
+            a.final_buf[w] = cur;
+        }
+        __syncthreads();
+    } else if (lane == 0) {
+        a.norms[w] = acc;
+        a.final_buf[w] = cur;
+    }
+}
+
+template <int P, int CK>
+__global__ void __launch_bounds__(BATCH_THREADS)
+k_batch_sweep(BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char bsm[];
+    __shared__ int s_q;
+    __shared__ double s_red[BATCH_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned char *wbase = bsm + (size_t)wid * Sweep<P, BATCH_R>::warp_bytes(a.K);
+    bool cta = true;   // uniform over the CTA until it leaves the big walks
+    for (;;) {
+        int q;
+        if (cta) {
+            __syncthreads();
+            if (threadIdx.x == 0) s_q = atomicAdd(&a.counter[0], 1);
+            __syncthreads();
+            q = s_q;
+            if (q >= a.nbig) { cta = false; continue; }
+        } else {
+            q = 0;
+            if (lane == 0) q = atomicAdd(&a.counter[1], 1);
+            q = a.nbig + __shfl_sync(0xffffffffu, q, 0);
+            if (q >= a.nwalks) return;
+        }
+        // one call site: one inlined copy of the walk code for both modes
+        run_walk_sweep<P, CK>(a, a.order[q], cta, cta ? (int)threadIdx.x : lane, cta ? (int)blockDim.x : 32,
+                              cta ? wid : 0, cta ? nw : 1, s_red, wbase);
+    }
+}
+
 }  // namespace qw
 
 using namespace qw;
@@ -174,10 +432,14 @@ struct qw_batch {
     int *order_dev = nullptr;
     float *P_dev = nullptr;
     double *norms_dev = nullptr;
-    int *counter = nullptr;
+    int *counter = nullptr;             // two queue counters (see BatchArgs)
     int *final_dev = nullptr;
-    int K = 32;
-    int grid = 0;
+    std::vector<double> work;           // light-cone site-steps of each walk
+    double split = 1e30;                // variant 1: CTA walks have more work than split x the mean per warp
+    int nbig = 0;
+    int K = 96;
+    int variant = 1;                    // 0: warp tiles with halos, 1: light-cone window sweep
+    int grid = 0, grid1 = 0;            // persistent grid of each variant (one wave)
     float cs[4] = {0, 0, 0, 0};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -196,22 +458,44 @@ static qw_status batch_cuda(qw_batch *b, cudaError_t e, const char *where) {
     return batch_fail(b, e == cudaErrorMemoryAllocation ? QW_ENOMEM : QW_ECUDA, m);
 }
 
+// The window sweep's shared memory: a chunk buffer and the k-level edge
+// buffer per warp.
+static size_t batch_smem(int prec, int variant, int K) {
+    if (variant != 1) return 0;
+    const size_t w = prec == QW_F32_BF16STORE ? Sweep<P_BF16, BATCH_R>::warp_bytes(K) : Sweep<P_F32, BATCH_R>::warp_bytes(K);
+    return w * (BATCH_THREADS / 32);
+}
+
+template <int P, int CK>
+static cudaError_t launch_batch_kernel(qw_batch *b, const BatchArgs &a, cudaStream_t s) {
+    if (b->variant == 1) {
+        const size_t smem = batch_smem(b->prec, 1, b->K);
+        cudaError_t e = cudaFuncSetAttribute(k_batch_sweep<P, CK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_batch_sweep<P, CK><<<b->grid1, BATCH_THREADS, smem, s>>>(a);
+    } else {
+        k_batch<P, CK><<<b->grid, BATCH_THREADS, 0, s>>>(a);
+    }
+    return cudaSuccess;
+}
+
 static cudaError_t batch_launch(qw_batch *b, cudaStream_t s) {
     BatchArgs a{};
     a.walks = b->walks_dev; a.order = b->order_dev; a.nwalks = b->nwalks;
     a.buf0 = b->buf[0]; a.buf1 = b->buf[1]; a.P = b->P_dev; a.norms = b->norms_dev;
     a.counter = b->counter; a.final_buf = b->final_dev; a.K = b->K; a.Ks = b->K;
     std::memcpy(a.cs, b->cs, sizeof a.cs);
-    cudaError_t e = cudaMemsetAsync(b->counter, 0, sizeof(int), s);
+    a.nbig = b->nbig;
+    cudaError_t e = cudaMemsetAsync(b->counter, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return e;
     if (b->prec == QW_F32_BF16STORE) {
-        if (b->kind == CK_REAL) k_batch<P_BF16, CK_REAL><<<b->grid, BATCH_THREADS, 0, s>>>(a);
-        else k_batch<P_BF16, CK_COMPLEX><<<b->grid, BATCH_THREADS, 0, s>>>(a);
+        if (b->kind == CK_REAL) e = launch_batch_kernel<P_BF16, CK_REAL>(b, a, s);
+        else e = launch_batch_kernel<P_BF16, CK_COMPLEX>(b, a, s);
     } else {
-        if (b->kind == CK_REAL) k_batch<P_F32, CK_REAL><<<b->grid, BATCH_THREADS, 0, s>>>(a);
-        else k_batch<P_F32, CK_COMPLEX><<<b->grid, BATCH_THREADS, 0, s>>>(a);
+        if (b->kind == CK_REAL) e = launch_batch_kernel<P_F32, CK_REAL>(b, a, s);
+        else e = launch_batch_kernel<P_F32, CK_COMPLEX>(b, a, s);
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // Per-walk drift factors (see WalkDesc): the whole correction alpha^-T is
@@ -223,6 +507,19 @@ static void set_gains(qw_batch *b, int K) {
         d.g_main = 1.f;
         d.g_last = (d.T <= 0 || d.alpha == 1.0) ? 1.f : (float)std::pow(d.alpha, -(double)d.T);
     }
+}
+
+// Variant 1: the walks whose light-cone work is at least `split` times the
+// mean work per resident warp run on a whole CTA (a prefix of the work-sorted
+// order); a single warp would be the critical path on them.
+static void set_split(qw_batch *b, double split) {
+    b->split = split;
+    double tot = 0.0;
+    for (double x : b->work) tot += x;
+    const double per_warp = tot / ((double)b->grid1 * (BATCH_THREADS / 32));
+    int n = 0;
+    while (n < b->nwalks && b->work[b->order[n]] >= split * per_warp) ++n;
+    b->nbig = n;
 }
 
 static void drop_graph(qw_batch *b) {
@@ -297,12 +594,13 @@ qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T, const 
     std::iota(b->order.begin(), b->order.end(), 0);
     // longest first by light-cone work, sum_{t<T} min(N, 2t+1) site-steps (the
     // tiles a walk actually computes), not by N*T
-    auto work = [&](int i) {
+    b->work.resize(nwalks);
+    for (int i = 0; i < nwalks; ++i) {
         const double n = (double)N[i], t = (double)T[i];
         const double tc = std::min(t, std::ceil((n - 1) / 2));   // steps before the cone covers the cycle
-        return tc * tc + (t - tc) * n;
-    };
-    std::stable_sort(b->order.begin(), b->order.end(), [&](int p, int q) { return work(p) > work(q); });
+        b->work[i] = tc * tc + (t - tc) * n;
+    }
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int p, int q) { return b->work[p] > b->work[q]; });
     const int slot = prec == QW_F32_BF16STORE ? 4 : 8;
     b->buf_bytes = (size_t)base * slot;
 
@@ -314,13 +612,21 @@ qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T, const 
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &per_sm, prec == QW_F32_BF16STORE ? (const void *)k_batch<P_BF16, CK_REAL> : (const void *)k_batch<P_F32, CK_REAL>,
             BATCH_THREADS, 0);
+    int per_sm1 = 0;
+    if (e == cudaSuccess) {
+        // the window sweep at the largest k it is planned with (the occupancy of smaller k is no lower)
+        const size_t smem = batch_smem(prec, 1, 8 * BATCH_R);
+        const void *f1 = prec == QW_F32_BF16STORE ? (const void *)k_batch_sweep<P_BF16, CK_REAL> : (const void *)k_batch_sweep<P_F32, CK_REAL>;
+        e = cudaFuncSetAttribute(f1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, f1, BATCH_THREADS, smem);
+    }
     if (e == cudaSuccess) e = dev_alloc(&b->buf[0], b->buf_bytes);
     if (e == cudaSuccess) e = dev_alloc(&b->buf[1], b->buf_bytes);
     if (e == cudaSuccess) e = dev_alloc((void **)&b->walks_dev, sizeof(WalkDesc) * nwalks);
     if (e == cudaSuccess) e = dev_alloc((void **)&b->order_dev, sizeof(int) * nwalks);
     if (e == cudaSuccess) e = dev_alloc((void **)&b->P_dev, sizeof(float) * (size_t)b->total_sites);
     if (e == cudaSuccess) e = dev_alloc((void **)&b->norms_dev, sizeof(double) * nwalks);
-    if (e == cudaSuccess) e = dev_alloc((void **)&b->counter, sizeof(int));
+    if (e == cudaSuccess) e = dev_alloc((void **)&b->counter, 2 * sizeof(int));
     if (e == cudaSuccess) e = dev_alloc((void **)&b->final_dev, sizeof(int) * nwalks);
     set_gains(b, b->K);
     if (e == cudaSuccess) e = cudaMemcpy(b->walks_dev, b->walks.data(), sizeof(WalkDesc) * nwalks, cudaMemcpyHostToDevice);
@@ -333,6 +639,8 @@ qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T, const 
         return st;
     }
     b->grid = std::max(1, std::min(nwalks, sms * std::max(1, per_sm)));
+    b->grid1 = std::max(1, std::min(nwalks, sms * std::max(1, per_sm1)));
+    set_split(b, b->split);
     *out = b;
     return QW_OK;
 }
@@ -377,6 +685,38 @@ qw_status qw_batch_get_plan(const qw_batch *b, int *depth_k, int *tile) {
     return QW_OK;
 }
 
+qw_status qw_batch_set_plan_ex(qw_batch *b, int depth_k, int variant) {
+    if (!b) return QW_EINVAL;
+    if (variant != 0 && variant != 1) return batch_fail(b, QW_EINVAL, "variant must be 0 (tiles) or 1 (window sweep)");
+    qw_status st = qw_batch_set_plan(b, depth_k);
+    if (st != QW_OK) return st;
+    if (variant != b->variant) {
+        cudaStreamSynchronize(b->stream);
+        drop_graph(b);   // the captured launch is one kernel variant
+        b->variant = variant;
+    }
+    return QW_OK;
+}
+
+qw_status qw_batch_set_split(qw_batch *b, double split) {
+    if (!b) return QW_EINVAL;
+    if (!(split >= 0.0)) return batch_fail(b, QW_EINVAL, "split must be >= 0");
+    cudaStreamSynchronize(b->stream);
+    drop_graph(b);   // the captured launch carries the split
+    set_split(b, split);
+    return QW_OK;
+}
+
+int qw_batch_cta_walks(const qw_batch *b) { return b ? b->nbig : -1; }
+
+qw_status qw_batch_get_plan_ex(const qw_batch *b, int *depth_k, int *tile, int *variant) {
+    if (!b || !depth_k || !tile || !variant) return QW_EINVAL;
+    *depth_k = b->K;
+    *tile = BATCH_R;
+    *variant = b->variant;
+    return QW_OK;
+}
+
 qw_status qw_batch_autotune(qw_batch *b, char *report, size_t report_len) {
     if (!b) return QW_EINVAL;
     const int ks[] = {8, 16, 24, 32, 48, 64, 96, 128};
@@ -384,26 +724,61 @@ qw_status qw_batch_autotune(qw_batch *b, char *report, size_t report_len) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int best_k = b->K;
+    int best_k = b->K, best_v = b->variant;
+    double best_split = b->split;
     cudaError_t e = cudaSuccess;
-    for (int k : ks) {
-        qw_status st = qw_batch_set_plan(b, k);
-        if (st != QW_OK) break;
-        if ((st = qw_batch_step(b)) != QW_OK) { e = cudaErrorUnknown; break; }   // capture + warm-up
+    // time the current plan (after a capturing warm-up run)
+    auto time_plan = [&](float &ms) -> bool {
+        if (qw_batch_step(b) != QW_OK) { e = cudaErrorUnknown; return false; }
         cudaEventRecord(e0, b->stream);
         qw_batch_step(b);
         cudaEventRecord(e1, b->stream);
-        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-        float ms = 0.f;
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return false;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) { best = ms; best_k = k; }
+        return true;
+    };
+    // variant 0 over k
+    for (int k : ks) {
+        float ms = 0.f;
+        if (qw_batch_set_plan_ex(b, k, 0) != QW_OK) { e = cudaErrorUnknown; break; }
+        if (!time_plan(ms)) break;
+        if (ms < best) { best = ms; best_k = k; best_v = 0; }
+    }
+    // variant 1: the CTA / single-warp split at k = 64 (0: every walk on a
+    // CTA; 1e30: none), then k at that split
+    double sp1 = b->split;
+    float best1 = 1e30f;
+    if (e == cudaSuccess && qw_batch_set_plan_ex(b, 64, 1) == QW_OK) {
+        for (double sp : {0.0, 0.125, 0.25, 0.5, 1.0, 1e30}) {
+            cudaStreamSynchronize(b->stream);
+            drop_graph(b);   // the captured launch carries the split
+            set_split(b, sp);
+            float ms = 0.f;
+            if (!time_plan(ms)) break;
+            if (ms < best1) { best1 = ms; sp1 = sp; }
+        }
+        cudaStreamSynchronize(b->stream);
+        drop_graph(b);
+        set_split(b, sp1);
+    }
+    for (int k : ks) {
+        if (e != cudaSuccess) break;
+        float ms = 0.f;
+        if (qw_batch_set_plan_ex(b, k, 1) != QW_OK) { e = cudaErrorUnknown; break; }
+        if (!time_plan(ms)) break;
+        if (ms < best) { best = ms; best_k = k; best_v = 1; best_split = sp1; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    set_split(b, best_split);
     if (e != cudaSuccess) return e == cudaErrorUnknown ? QW_ECUDA : batch_cuda(b, e, "batch autotune");
-    qw_batch_set_plan(b, best_k);
+    qw_batch_set_plan_ex(b, best_k, best_v);
     if (report && report_len) {
-        std::snprintf(report, report_len, "{\"tuned\": true, \"k\": %d, \"tile\": %d, \"ms\": %.6g}", best_k, BATCH_R, best);
+        std::snprintf(report, report_len,
+                      "{\"tuned\": true, \"k\": %d, \"tile\": %d, \"variant\": \"%s\", \"cta_walks\": %d, "
+                      "\"ms\": %.6g}", best_k, BATCH_R, best_v ? "window_sweep" : "tiles", best_v ? b->nbig : b->nwalks, best);
     }
     return QW_OK;
 }

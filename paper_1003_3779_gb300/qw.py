@@ -75,6 +75,10 @@ def lib():
         "qw_batch_set_plan": (I, [P, I]),
         "qw_batch_get_plan": (I, [P, P, P]),
         "qw_batch_autotune": (I, [P, ctypes.c_char_p, S]),
+        "qw_batch_set_plan_ex": (I, [P, I, I]),
+        "qw_batch_set_split": (I, [P, ctypes.c_double]),
+        "qw_batch_cta_walks": (I, [P]),
+        "qw_batch_get_plan_ex": (I, [P, P, P, P]),
         "qw_status_string": (ctypes.c_char_p, [I]),
         "qw_last_error": (ctypes.c_char_p, [P]),
         "qw_batch_last_error": (ctypes.c_char_p, [P]),
@@ -408,6 +412,27 @@ class Batch:
         k, t = ctypes.c_int(), ctypes.c_int()
         _check(lib().qw_batch_get_plan(self.h, ctypes.byref(k), ctypes.byref(t)), self.h, batch=True)
         return k.value, t.value
+
+    def set_plan_ex(self, k, variant):
+        """variant 0: warp tiles with halos; 1: light-cone window sweep."""
+        _check(lib().qw_batch_set_plan_ex(self.h, int(k), int(variant)), self.h, batch=True)
+        return self
+
+    def set_split(self, split):
+        """Variant 1: walks with more light-cone work than split x the mean per
+        resident warp run on a whole CTA, the rest on one warp each (0: all on
+        CTAs; inf: all on warps)."""
+        _check(lib().qw_batch_set_split(self.h, min(float(split), 1e300)), self.h, batch=True)
+        return self
+
+    def cta_walks(self):
+        return int(lib().qw_batch_cta_walks(self.h))
+
+    def plan_ex(self):
+        k, t, v = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().qw_batch_get_plan_ex(self.h, ctypes.byref(k), ctypes.byref(t), ctypes.byref(v)),
+               self.h, batch=True)
+        return k.value, t.value, v.value
 
     def autotune(self):
         buf = ctypes.create_string_buffer(256)

@@ -43,11 +43,24 @@ def small_batch(seed, n):
     return N, T, coins, x0
 
 
+# (variant, split): warp tiles; the window sweep with every walk on one warp,
+# every walk on a CTA, and a mix
+PLANS = [(0, None), (1, float("inf")), (1, 0.0), (1, 1.0)]
+
+
+@pytest.mark.parametrize("variant,split", PLANS)
 @pytest.mark.parametrize("prec,k", [("f32", 1), ("f32", 7), ("f32", 32), ("f32", 128),
                                     ("bf16", 32), ("bf16", 128)])
-def test_batch_matches_oracle_per_walk(qw, prec, k):
+def test_batch_matches_oracle_per_walk(qw, prec, k, variant, split):
     N, T, coins, x0 = small_batch(1, 24)
-    b = qw.Batch(N, T, coins, x0, CS, prec=prec).set_plan(k)
+    b = qw.Batch(N, T, coins, x0, CS, prec=prec).set_plan_ex(k, variant)
+    if split is not None:
+        b.set_split(split)
+        ncta = b.cta_walks()
+        assert ncta == (24 if split == 0 else 0 if split == float("inf") else ncta)
+        if split == 1.0:
+            assert 0 < ncta < 24
+    assert b.plan_ex() == (k, 16, variant)
     b.step()
     P, norms = b.probabilities()
     for i in range(len(N)):
@@ -62,11 +75,12 @@ def test_batch_matches_oracle_per_walk(qw, prec, k):
     b.close()
 
 
-def test_batch_complex_coins_and_repeat(qw):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_batch_complex_coins_and_repeat(qw, variant):
     rng = np.random.default_rng(2)
     N, T, _, x0 = small_batch(3, 16)
     coins = np.stack([inputs.random_unitary(2, rng) for _ in range(16)])
-    b = qw.Batch(N, T, coins, x0, CS, prec="f32")
+    b = qw.Batch(N, T, coins, x0, CS, prec="f32").set_plan_ex(32, variant)
     b.step()
     P1, n1 = b.probabilities()
     P1 = P1.copy()
@@ -79,20 +93,47 @@ def test_batch_complex_coins_and_repeat(qw):
     b.close()
 
 
-def test_light_cone_zeros_are_exact(qw):
-    N = np.array([60000, 40000, 65536])
-    T = np.array([100, 1000, 2000])
-    x0 = np.array([5, 39990, 30000])
-    coins = np.stack([inputs.su2(0.4)] * 3)
-    b = qw.Batch(N, T, coins, x0, CS)
+@pytest.mark.parametrize("variant,split", PLANS)
+def test_light_cone_zeros_are_exact(qw, variant, split):
+    """Cones that wrap past site 0 and past site N-1, one that does not, and an
+    odd N whose cone reaches round the cycle (window and whole-cycle passes)."""
+    N = np.array([60000, 40000, 65536, 50001, 3001])
+    T = np.array([100, 1000, 2000, 3, 1700])
+    x0 = np.array([5, 39990, 30000, 50000, 17])
+    coins = np.stack([inputs.su2(0.4)] * 5)
+    b = qw.Batch(N, T, coins, x0, CS).set_plan_ex(64, variant)
+    if split is not None:
+        b.set_split(split)
     b.step()
     P, _ = b.probabilities()
-    for i in range(3):
+    for i in range(5):
         Pi = P[b.offsets[i]:b.offsets[i + 1]]
         dist = np.minimum((np.arange(N[i]) - x0[i]) % N[i], (x0[i] - np.arange(N[i])) % N[i])
         assert np.all(Pi[dist > T[i]] == 0.0)
         assert Pi[dist <= T[i]].sum() > 0.999
+        want = oracle_walk(int(N[i]), int(T[i]), coins[i], int(x0[i]))
+        assert maxabs(b.state(i), want) < amp_tol("f32", int(T[i])), i
     b.close()
+
+
+def test_batch_variants_agree_and_reject_unknown(qw):
+    N, T, coins, x0 = small_batch(6, 12)
+    out = []
+    for v, sp in PLANS:
+        b = qw.Batch(N, T, coins, x0, CS).set_plan_ex(48, v)
+        if sp is not None:
+            b.set_split(sp)
+        b.step()
+        out.append(b.probabilities()[0].copy())
+        if v == 1:
+            with pytest.raises(qw.QWError):
+                b.set_plan_ex(48, 2)
+            with pytest.raises(qw.QWError):
+                b.set_split(-1.0)
+        b.close()
+    assert np.abs(out[0] - out[1]).max() < 1e-6
+    # the sweep's CTA segments and single warps give the same bits
+    assert np.array_equal(out[1], out[2]) and np.array_equal(out[1], out[3])
 
 
 def test_autotune_batch(qw):
@@ -102,6 +143,7 @@ def test_autotune_batch(qw):
     assert '"tuned": true' in rep
     k, tile = b.plan()
     assert 8 <= k <= 128 and tile == 16
+    assert b.plan_ex()[2] in (0, 1)
     b.step()
     _, norms = b.probabilities()
     assert np.abs(norms - 1).max() < 1e-5
@@ -109,12 +151,13 @@ def test_autotune_batch(qw):
 
 
 @pytest.mark.slow
-def test_full_batch_4096_sampled(qw):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_full_batch_4096_sampled(qw, variant):
     """The full batched workload (4096 walks, N~U[256,65536], T~U[64,4096]):
     every norm is 1, and sampled walks equal the oracle run on their own."""
     N, T, theta, x0 = inputs.batch_1d_params()
     coins = np.stack([inputs.su2(th) for th in theta])
-    b = qw.Batch(N, T, coins, x0, CS)
+    b = qw.Batch(N, T, coins, x0, CS).set_plan_ex(64, variant)
     b.step()
     P, norms = b.probabilities()
     # FP32 bound T * 4u per walk: walks whose coin is within ~2^-20 of diagonal
