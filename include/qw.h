@@ -261,15 +261,14 @@ qw_status qw_batch_get_plan(const qw_batch *b, int *depth_k, int *tile);
 qw_status qw_batch_set_plan_ex(qw_batch *b, int depth_k, int variant);
 qw_status qw_batch_get_plan_ex(const qw_batch *b, int *depth_k, int *tile, int *variant);
 
-/* Work split of variant 1: a walk whose light-cone work sum_{t<T} min(N, 2t+1)
- * (site-steps) is at least `split` times the batch's mean work per resident warp
- * is shared by the four warps of a CTA (segments with warm-up chunks, a
- * barrier between passes); every other walk is swept by one warp alone.  0
- * puts every walk on a CTA; a huge value (the default, 1e30) every walk on a
- * warp.  Results do not depend on it.  QW_EINVAL for a negative or NaN value;
- * re-captures the graph.  qw_batch_cta_walks: how many walks run on a CTA
- * (-1 for a null handle). */
-qw_status qw_batch_set_split(qw_batch *b, double split);
+/* Work split of variant 1: the n walks with the most light-cone work
+ * sum_{t<T} min(N, 2t+1) (site-steps) are each shared by the four warps of a
+ * CTA (segments with warm-up chunks, a barrier between passes), which
+ * shortens the longest walks, the critical path; every other walk is swept by
+ * one warp alone.  n is clamped to [0, nwalks]; the default is nwalks / 16.
+ * Results do not depend on it.  QW_EINVAL for n < 0; re-captures the graph.
+ * qw_batch_cta_walks returns n (-1 for a null handle). */
+qw_status qw_batch_set_cta_walks(qw_batch *b, int n);
 int qw_batch_cta_walks(const qw_batch *b);
 
 /* Time the batch for k in {8, ..., 128} and both variants (each timing runs

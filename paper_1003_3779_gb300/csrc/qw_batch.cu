@@ -347,8 +347,9 @@ __device__ __forceinline__ void run_walk_sweep(const BatchArgs &a, int w, bool c
             L = 0;
             nch = (int)((d.n + B - 1) / B);
         }
-        // on a CTA, segments of at least two chunks, at most one per warp
-        const int nseg = max(1, min(nw, nch / 2));
+        // on a CTA, one segment per warp (down to one chunk each): the CTA walks
+        // are the critical path, so the extra warm-up chunks buy a shorter pass
+        const int nseg = max(1, min(nw, nch));
         const float gl = (t0 + k >= d.T) ? d.g_last : d.g_main;
         if (wid < nseg) {
             const int j0 = (int)((int64_t)nch * wid / nseg), j1 = (int)((int64_t)nch * (wid + 1) / nseg);
@@ -435,8 +436,7 @@ struct qw_batch {
     int *counter = nullptr;             // two queue counters (see BatchArgs)
     int *final_dev = nullptr;
     std::vector<double> work;           // light-cone site-steps of each walk
-    double split = 1e30;                // variant 1: CTA walks have more work than split x the mean per warp
-    int nbig = 0;
+    int nbig = 0;                       // variant 1: the nbig walks with the most work run on a CTA
     int K = 96;
     int variant = 1;                    // 0: warp tiles with halos, 1: light-cone window sweep
     int grid = 0, grid1 = 0;            // persistent grid of each variant (one wave)
@@ -507,19 +507,6 @@ static void set_gains(qw_batch *b, int K) {
         d.g_main = 1.f;
         d.g_last = (d.T <= 0 || d.alpha == 1.0) ? 1.f : (float)std::pow(d.alpha, -(double)d.T);
     }
-}
-
-// Variant 1: the walks whose light-cone work is at least `split` times the
-// mean work per resident warp run on a whole CTA (a prefix of the work-sorted
-// order); a single warp would be the critical path on them.
-static void set_split(qw_batch *b, double split) {
-    b->split = split;
-    double tot = 0.0;
-    for (double x : b->work) tot += x;
-    const double per_warp = tot / ((double)b->grid1 * (BATCH_THREADS / 32));
-    int n = 0;
-    while (n < b->nwalks && b->work[b->order[n]] >= split * per_warp) ++n;
-    b->nbig = n;
 }
 
 static void drop_graph(qw_batch *b) {
@@ -640,7 +627,7 @@ qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T, const 
     }
     b->grid = std::max(1, std::min(nwalks, sms * std::max(1, per_sm)));
     b->grid1 = std::max(1, std::min(nwalks, sms * std::max(1, per_sm1)));
-    set_split(b, b->split);
+    b->nbig = nwalks / 16;   // the largest sixteenth on CTAs (the autotuner refines it)
     *out = b;
     return QW_OK;
 }
@@ -698,12 +685,15 @@ qw_status qw_batch_set_plan_ex(qw_batch *b, int depth_k, int variant) {
     return QW_OK;
 }
 
-qw_status qw_batch_set_split(qw_batch *b, double split) {
+qw_status qw_batch_set_cta_walks(qw_batch *b, int n) {
     if (!b) return QW_EINVAL;
-    if (!(split >= 0.0)) return batch_fail(b, QW_EINVAL, "split must be >= 0");
-    cudaStreamSynchronize(b->stream);
-    drop_graph(b);   // the captured launch carries the split
-    set_split(b, split);
+    if (n < 0) return batch_fail(b, QW_EINVAL, "the number of CTA walks must be >= 0");
+    n = std::min(n, b->nwalks);
+    if (n != b->nbig) {
+        cudaStreamSynchronize(b->stream);
+        drop_graph(b);   // the captured launch carries the split
+        b->nbig = n;
+    }
     return QW_OK;
 }
 
@@ -725,7 +715,7 @@ qw_status qw_batch_autotune(qw_batch *b, char *report, size_t report_len) {
     cudaEventCreate(&e1);
     float best = 1e30f;
     int best_k = b->K, best_v = b->variant;
-    double best_split = b->split;
+    int best_n = b->nbig;
     cudaError_t e = cudaSuccess;
     // time the current plan (after a capturing warm-up run)
     auto time_plan = [&](float &ms) -> bool {
@@ -744,35 +734,30 @@ qw_status qw_batch_autotune(qw_batch *b, char *report, size_t report_len) {
         if (!time_plan(ms)) break;
         if (ms < best) { best = ms; best_k = k; best_v = 0; }
     }
-    // variant 1: the CTA / single-warp split at k = 64 (0: every walk on a
-    // CTA; 1e30: none), then k at that split
-    double sp1 = b->split;
+    // variant 1: how many of the largest walks run on CTAs (the rest on single
+    // warps), at k = 96, then k at that split
+    int n1 = b->nbig;
     float best1 = 1e30f;
-    if (e == cudaSuccess && qw_batch_set_plan_ex(b, 64, 1) == QW_OK) {
-        for (double sp : {0.0, 0.125, 0.25, 0.5, 1.0, 1e30}) {
-            cudaStreamSynchronize(b->stream);
-            drop_graph(b);   // the captured launch carries the split
-            set_split(b, sp);
+    if (e == cudaSuccess && qw_batch_set_plan_ex(b, 96, 1) == QW_OK) {
+        for (int n : {0, 16, 32, 64, 128, 256, 512, 1024, b->nwalks}) {
+            if (n > b->nwalks) continue;
+            qw_batch_set_cta_walks(b, n);
             float ms = 0.f;
             if (!time_plan(ms)) break;
-            if (ms < best1) { best1 = ms; sp1 = sp; }
+            if (ms < best1) { best1 = ms; n1 = n; }
         }
-        cudaStreamSynchronize(b->stream);
-        drop_graph(b);
-        set_split(b, sp1);
+        qw_batch_set_cta_walks(b, n1);
     }
     for (int k : ks) {
         if (e != cudaSuccess) break;
         float ms = 0.f;
         if (qw_batch_set_plan_ex(b, k, 1) != QW_OK) { e = cudaErrorUnknown; break; }
         if (!time_plan(ms)) break;
-        if (ms < best) { best = ms; best_k = k; best_v = 1; best_split = sp1; }
+        if (ms < best) { best = ms; best_k = k; best_v = 1; best_n = n1; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaStreamSynchronize(b->stream);
-    drop_graph(b);
-    set_split(b, best_split);
+    qw_batch_set_cta_walks(b, best_n);
     if (e != cudaSuccess) return e == cudaErrorUnknown ? QW_ECUDA : batch_cuda(b, e, "batch autotune");
     qw_batch_set_plan_ex(b, best_k, best_v);
     if (report && report_len) {

@@ -76,7 +76,7 @@ def lib():
         "qw_batch_get_plan": (I, [P, P, P]),
         "qw_batch_autotune": (I, [P, ctypes.c_char_p, S]),
         "qw_batch_set_plan_ex": (I, [P, I, I]),
-        "qw_batch_set_split": (I, [P, ctypes.c_double]),
+        "qw_batch_set_cta_walks": (I, [P, I]),
         "qw_batch_cta_walks": (I, [P]),
         "qw_batch_get_plan_ex": (I, [P, P, P, P]),
         "qw_status_string": (ctypes.c_char_p, [I]),
@@ -418,11 +418,10 @@ class Batch:
         _check(lib().qw_batch_set_plan_ex(self.h, int(k), int(variant)), self.h, batch=True)
         return self
 
-    def set_split(self, split):
-        """Variant 1: walks with more light-cone work than split x the mean per
-        resident warp run on a whole CTA, the rest on one warp each (0: all on
-        CTAs; inf: all on warps)."""
-        _check(lib().qw_batch_set_split(self.h, min(float(split), 1e300)), self.h, batch=True)
+    def set_cta_walks(self, n):
+        """Variant 1: the n walks with the most light-cone work run on a whole
+        CTA each, the rest on one warp each."""
+        _check(lib().qw_batch_set_cta_walks(self.h, int(n)), self.h, batch=True)
         return self
 
     def cta_walks(self):

@@ -43,23 +43,20 @@ def small_batch(seed, n):
     return N, T, coins, x0
 
 
-# (variant, split): warp tiles; the window sweep with every walk on one warp,
-# every walk on a CTA, and a mix
-PLANS = [(0, None), (1, float("inf")), (1, 0.0), (1, 1.0)]
+# (variant, CTA walks): warp tiles; the window sweep with every walk on one
+# warp, every walk on a CTA, and a mix
+PLANS = [(0, None), (1, 0), (1, 1 << 20), (1, 7)]
 
 
-@pytest.mark.parametrize("variant,split", PLANS)
+@pytest.mark.parametrize("variant,ncta", PLANS)
 @pytest.mark.parametrize("prec,k", [("f32", 1), ("f32", 7), ("f32", 32), ("f32", 128),
                                     ("bf16", 32), ("bf16", 128)])
-def test_batch_matches_oracle_per_walk(qw, prec, k, variant, split):
+def test_batch_matches_oracle_per_walk(qw, prec, k, variant, ncta):
     N, T, coins, x0 = small_batch(1, 24)
     b = qw.Batch(N, T, coins, x0, CS, prec=prec).set_plan_ex(k, variant)
-    if split is not None:
-        b.set_split(split)
-        ncta = b.cta_walks()
-        assert ncta == (24 if split == 0 else 0 if split == float("inf") else ncta)
-        if split == 1.0:
-            assert 0 < ncta < 24
+    if ncta is not None:
+        b.set_cta_walks(ncta)
+        assert b.cta_walks() == min(ncta, 24)
     assert b.plan_ex() == (k, 16, variant)
     b.step()
     P, norms = b.probabilities()
@@ -93,8 +90,8 @@ def test_batch_complex_coins_and_repeat(qw, variant):
     b.close()
 
 
-@pytest.mark.parametrize("variant,split", PLANS)
-def test_light_cone_zeros_are_exact(qw, variant, split):
+@pytest.mark.parametrize("variant,ncta", PLANS)
+def test_light_cone_zeros_are_exact(qw, variant, ncta):
     """Cones that wrap past site 0 and past site N-1, one that does not, and an
     odd N whose cone reaches round the cycle (window and whole-cycle passes)."""
     N = np.array([60000, 40000, 65536, 50001, 3001])
@@ -102,8 +99,8 @@ def test_light_cone_zeros_are_exact(qw, variant, split):
     x0 = np.array([5, 39990, 30000, 50000, 17])
     coins = np.stack([inputs.su2(0.4)] * 5)
     b = qw.Batch(N, T, coins, x0, CS).set_plan_ex(64, variant)
-    if split is not None:
-        b.set_split(split)
+    if ncta is not None:
+        b.set_cta_walks(ncta)
     b.step()
     P, _ = b.probabilities()
     for i in range(5):
@@ -122,14 +119,14 @@ def test_batch_variants_agree_and_reject_unknown(qw):
     for v, sp in PLANS:
         b = qw.Batch(N, T, coins, x0, CS).set_plan_ex(48, v)
         if sp is not None:
-            b.set_split(sp)
+            b.set_cta_walks(sp)
         b.step()
         out.append(b.probabilities()[0].copy())
         if v == 1:
             with pytest.raises(qw.QWError):
                 b.set_plan_ex(48, 2)
             with pytest.raises(qw.QWError):
-                b.set_split(-1.0)
+                b.set_cta_walks(-1)
         b.close()
     assert np.abs(out[0] - out[1]).max() < 1e-6
     # the sweep's CTA segments and single warps give the same bits
