@@ -41,6 +41,23 @@ __device__ __forceinline__ void coin4g(const CoinP<R> &cp, const Cx<R> (&a)[4], 
     }
 }
 
+// Rows of psi_0 in flight per warp: each row is cp.async-copied into a ring
+// of shared-memory slots TB_RING - 1 rows before it is needed, so the global
+// latency hides behind that many rows of compute (one row, about the time of
+// the KT levels, is not enough).  Each lane copies and reads back only its own
+// 16 bytes per plane.
+constexpr int TB_RING = 4;
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait_pending() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Dynamic shared memory of one 128-thread block.
+inline size_t step2d_tb_smem() { return (size_t)(128 / 32) * TB_RING * 4 * 32 * 16; }
+
 template <int P, int KT, int CK, int FF>
 __global__ void __launch_bounds__(128)
 k_step2d_tb(View in, View out, int64_t nx, int64_t ny, int64_t W, int64_t nstrips, int64_t H, int64_t nchunks,
@@ -49,7 +66,9 @@ k_step2d_tb(View in, View out, int64_t nx, int64_t ny, int64_t W, int64_t nstrip
     using real = typename S::real;
     using C = Cx<real>;
     constexpr int R = 2;   // sites per lane (one 16-byte vector per plane in FP32)
-    static_assert(R % S::VEC == 0 || S::VEC % R == 0, "lane run and vector width must nest");
+    static_assert(P == P_F32 && R * S::SLOT_BYTES == 16, "one 16-byte ring slot per lane and plane");
+    extern __shared__ __align__(16) unsigned char tsm[];
+    uint4 *ring = reinterpret_cast<uint4 *>(tsm) + (size_t)(threadIdx.x >> 5) * TB_RING * 4 * 32;   // [slot][plane][lane]
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gw >= nstrips * nchunks) return;   // uniform per warp
@@ -78,36 +97,43 @@ k_step2d_tb(View in, View out, int64_t nx, int64_t ny, int64_t W, int64_t nstrip
     if constexpr (CK == CK_HH) gain = gain * (real)(1.0 / (double)(1u << KT));   // the factors 1/2 of H (x) H
     const bool gain_one = is_one(gain);
 
-    // psi_0 of the next row is loaded one iteration ahead, so its latency hides
-    // behind the KT levels of the current row
     // rows stay within one period of the torus (H <= ny, KT < ny is not needed:
     // q is at most one period outside [0, ny)), so a conditional add wraps them
     auto wrap_row = [&](int64_t q) { return q < 0 ? q + ny * ((-q + ny - 1) / ny) : (q >= ny ? q % ny : q); };
-    auto load_row = [&](int64_t q, C (&a)[4][R]) {
-        const int64_t row = wrap_row(q) * nx;
+    const int64_t qbeg = y0 - KT, qend = y0 + hthis + KT;
+    // copy row q of psi_0 (this lane's R sites of each plane) into its ring slot;
+    // one commit group per row, empty past the end, so the waits count rows
+    auto issue_row = [&](int64_t q) {
+        if (q < qend) {
+            const int64_t row = wrap_row(q) * nx;
+            uint4 *dst = ring + (int)((q - qbeg) % TB_RING) * 4 * 32 + lane;
+            const char *base = static_cast<const char *>(in.p);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            if (vec) {
+            for (int c = 0; c < 4; ++c) {
+                if (vec) {
+                    cp_async16(dst + c * 32, base + (c * in.pitch + row + xs) * S::SLOT_BYTES);
+                } else {
 #pragma unroll
-                for (int i = 0; i < R; i += S::VEC) S::ldv(in, c, row + xs + i, &a[c][i]);
-            } else {
-#pragma unroll
-                for (int i = 0; i < R; ++i) a[c][i] = S::ld(in, c, row + cx[i]);
+                    for (int i = 0; i < R; ++i)
+                        cp_async8(reinterpret_cast<unsigned char *>(dst + c * 32) + i * S::SLOT_BYTES,
+                                  base + (c * in.pitch + row + cx[i]) * S::SLOT_BYTES);
+                }
             }
         }
+        cp_async_commit();
     };
-    C nxt[4][R];
-    load_row(y0 - KT, nxt);
-    for (int64_t q = y0 - KT; q < y0 + hthis + KT; ++q) {
+#pragma unroll
+    for (int r = 0; r < TB_RING - 1; ++r) issue_row(qbeg + r);
+    for (int64_t q = qbeg; q < qend; ++q) {
         // psi_0 of row q with the coin applied: the newest input of level 1
         C N[R][4];
         {
+            issue_row(q + TB_RING - 1);
+            cp_async_wait_pending<TB_RING - 1>();   // row q has landed
             C a[4][R];
+            const uint4 *src = ring + (int)((q - qbeg) % TB_RING) * 4 * 32 + lane;
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-#pragma unroll
-                for (int i = 0; i < R; ++i) a[c][i] = nxt[c][i];
-            if (q + 1 < y0 + hthis + KT) load_row(q + 1, nxt);
+            for (int c = 0; c < 4; ++c) S::unpack(src[c * 32], &a[c][0]);
 #pragma unroll
             for (int i = 0; i < R; ++i) {
                 C ai[4] = {a[0][i], a[1][i], a[2][i], a[3][i]}, pi[4];

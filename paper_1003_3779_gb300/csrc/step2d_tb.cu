@@ -23,8 +23,8 @@ static cudaError_t go2d_tb(const Step2DArgs &a, const CoinP<float> &cp, cudaStre
     const int64_t nchunks = (a.ny + H - 1) / H;
     const int64_t nwarps = nstrips * nchunks;
     const int64_t blocks = (nwarps + 3) / 4;
-    k_step2d_tb<P_F32, KT, CK, FF><<<(unsigned)blocks, 128, 0, s>>>(a.in, a.out, a.nx, a.ny, W, nstrips, H, nchunks,
-                                                                   cp, (float)a.gain);
+    k_step2d_tb<P_F32, KT, CK, FF><<<(unsigned)blocks, 128, step2d_tb_smem(), s>>>(a.in, a.out, a.nx, a.ny, W, nstrips,
+                                                                                 H, nchunks, cp, (float)a.gain);
     return cudaGetLastError();
 }
 
