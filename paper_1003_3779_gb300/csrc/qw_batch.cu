@@ -653,7 +653,8 @@ qw_status qw_batch_step(qw_batch *b) {
 
 qw_status qw_batch_set_plan(qw_batch *b, int depth_k) {
     if (!b) return QW_EINVAL;
-    if (depth_k < 1 || depth_k > 8 * BATCH_R) return batch_fail(b, QW_EINVAL, "k must be in [1, 128]");
+    if (depth_k < 1 || depth_k > 8 * BATCH_R)
+        return batch_fail(b, QW_EINVAL, "k must be in [1, " + std::to_string(8 * BATCH_R) + "]");
     if (depth_k != b->K) {
         cudaStreamSynchronize(b->stream);
         drop_graph(b);   // the captured launch carries k
@@ -729,6 +730,7 @@ qw_status qw_batch_autotune(qw_batch *b, char *report, size_t report_len) {
     };
     // variant 0 over k
     for (int k : ks) {
+        if (k > 8 * BATCH_R) break;
         float ms = 0.f;
         if (qw_batch_set_plan_ex(b, k, 0) != QW_OK) { e = cudaErrorUnknown; break; }
         if (!time_plan(ms)) break;
@@ -738,7 +740,7 @@ qw_status qw_batch_autotune(qw_batch *b, char *report, size_t report_len) {
     // warps), at k = 96, then k at that split
     int n1 = b->nbig;
     float best1 = 1e30f;
-    if (e == cudaSuccess && qw_batch_set_plan_ex(b, 96, 1) == QW_OK) {
+    if (e == cudaSuccess && qw_batch_set_plan_ex(b, std::min(96, 8 * BATCH_R), 1) == QW_OK) {
         for (int n : {0, 16, 32, 64, 128, 256, 512, 1024, b->nwalks}) {
             if (n > b->nwalks) continue;
             qw_batch_set_cta_walks(b, n);
@@ -749,7 +751,7 @@ qw_status qw_batch_autotune(qw_batch *b, char *report, size_t report_len) {
         qw_batch_set_cta_walks(b, n1);
     }
     for (int k : ks) {
-        if (e != cudaSuccess) break;
+        if (e != cudaSuccess || k > 8 * BATCH_R) break;
         float ms = 0.f;
         if (qw_batch_set_plan_ex(b, k, 1) != QW_OK) { e = cudaErrorUnknown; break; }
         if (!time_plan(ms)) break;
