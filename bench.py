@@ -452,15 +452,19 @@ def run_gpu(args, rank, world, local):
         barrier(dist, local)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        marks = []
         for _ in range(n_e2e):
             qw.qw_set_state(w.h, hin)
             qw.qw_step(w.h, T_STEPS)
-            qw.qw_probabilities(w.h, hP)
+            qw.qw_probabilities(w.h, hP)   # synchronises: the host holds the step's P
+            marks.append(time.perf_counter())
         torch.cuda.synchronize()
         te = max_over_ranks(dist, time.perf_counter() - t0, local)
+        per_step = [1e3 * (b - a) for a, b in zip([t0] + marks[:-1], marks)]
         e2e = {"value": aggregate_throughput(2.0 * N_SITES * T_STEPS * n_e2e, te, world),
                "unit": UNIT, "h2d_bytes_per_step": int(hin.nbytes),
-               "d2h_bytes_per_step": int(hP.nbytes) + 8, "steps": n_e2e}
+               "d2h_bytes_per_step": int(hP.nbytes) + 8, "steps": n_e2e,
+               "ms_per_step": [round(x, 2) for x in per_step]}
         del host_in, host_P
     w.close()
     return {
