@@ -119,11 +119,30 @@ static void tiles_of(int prec, int &a, int &b) {
     else { a = 8; b = 16; }
 }
 
+// Warps the 2D streaming kernel can keep busy at depth KT: 64-column strips
+// with KT columns of halo per side, row chunks of at least 8 KT rows.
+static int64_t tb_warps(const qw_walk *w, int KT) {
+    const int64_t W = 64 - 2 * KT;
+    return ((w->nx + W - 1) / W) * ((w->ny + 8 * KT - 1) / (8 * KT));
+}
+
 static void default_plan(const qw_walk *w, int &k, int &tile, int &variant) {
     variant = 0;
     if (w->ndim == 2) {
+        // the streaming kernel where the lattice gives it two waves of warps
+        // (8 per SM), else the fused single step
         tile = 0;
-        k = (w->bc == QW_BC_PERIODIC && !w->has_links && step2d_tb_ok(w->prec, w->kind, 8, w->shift)) ? 8 : 1;
+        k = 1;
+        if (w->bc != QW_BC_PERIODIC || w->has_links) return;
+        static int sms = 0;
+        if (!sms) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+        }
+        const int64_t enough = (int64_t)sms * 8 * 2;
+        for (int KT : {8, 4})
+            if (step2d_tb_ok(w->prec, w->kind, KT, w->shift) && tb_warps(w, KT) >= enough) { k = KT; break; }
         return;
     }
     switch (w->prec) {
