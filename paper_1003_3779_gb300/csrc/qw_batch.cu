@@ -1,27 +1,34 @@
 // qw_batch.cu -- many independent walks on cycles in one persistent launch.
 //
 // Each walk is the 1D walk of Sec. 2.2 (cycle Z_N, coin dim 2, U = S (I (x) C)
-// of Sec. 2.1) with its own N, T and 2x2 coin, started localised at x0.  One
-// CTA owns one walk at a time: it pops the next walk from a global counter
-// (walks sorted by light-cone work, largest first), zeroes the walk's two state buffers,
-// places the initial amplitude, and advances the walk k steps per round with
-// the same warp register-tile kernel as the single cycle (tb_tile), its four
-// warps sharing the tiles of the walk and meeting at a __syncthreads between
-// rounds.  The walk's state ping-pongs between two global buffers; a walk of
-// at most 65536 sites is 1 MiB per buffer in FP32 (0.5 MiB in bfloat16), so it
-// mostly stays in L2 while its CTA works on it.
+// of Sec. 2.1) with its own N, T and 2x2 coin, started localised at x0.  The
+// walks are sorted by light-cone work, largest first, and popped from global
+// counters by persistent CTAs or warps, which zero the walk's two state
+// buffers, place the initial amplitude and advance the walk k steps per round.
+// The walk's state ping-pongs between two global buffers; a walk of at most
+// 65536 sites is 1 MiB per buffer in FP32 (0.5 MiB in bfloat16), so it mostly
+// stays in L2 while it is worked on.  Two kernels:
+//
+// - k_batch (variant 0): one CTA per walk; its four warps share the register
+//   tiles (tb_tile, with a halo of k sites per side) of a round and meet at a
+//   __syncthreads between rounds.
+// - k_batch_sweep (variant 1): the time-skewed sweep of the single cycle over
+//   the chunks that cover the walk's light cone, with no halo.  The largest
+//   walks run on a CTA's four warps as segments; the rest on single warps.
 //
 // Light cone (Sec. 3, the "line" computation window): after t steps from a
-// single site x0 the state is zero outside [x0 - t, x0 + t].  A tile whose
-// outputs all lie outside the cone of the current round is skipped; its
-// buffer region is still the zero written at the start.  (Shorter rounds while
-// the cone is narrow clip it more tightly but cost more per-round traffic and
+// single site x0 the state is zero outside [x0 - t, x0 + t].  Variant 0 skips
+// the tiles whose outputs all lie outside the cone of the current round (their
+// buffer region is still the zero written at the start); variant 1 sweeps only
+// the window from the cone's left end.  (Shorter rounds while the cone is
+// narrow clip it more tightly but cost more per-round traffic and
 // synchronisation than they save on this workload: measured 28 ms against
-// 17 ms for 4096 walks, so a single k is used; Ks stays available.)
+// 17 ms for 4096 walks in variant 0, so a single k is used; Ks stays
+// available.)
 //
-// At the end of its walk the CTA writes P(x) = |psi0|^2 + |psi1|^2 (float) and
-// the walk's norm (double, fixed order) to the batch outputs.  There are no
-// waits other than __syncthreads: nothing spins.
+// At the end of its walk the group writes P(x) = |psi0|^2 + |psi1|^2 (float)
+// and the walk's norm (double, fixed order) to the batch outputs.  There are
+// no waits other than __syncthreads / __syncwarp: nothing spins.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
