@@ -1,0 +1,79 @@
+"""Full-size parity in the configurations the benchmark times, on sampled sites.
+
+A site's amplitudes after T steps depend only on the initial state within T
+sites of it (the light cone), so the FP64 oracle run on the window of 2T + 1
+sites around a sampled site, with an absorbing edge, gives that site's exact
+value; the values outside the window reach the edge after T steps at the
+earliest and never the centre.  The tolerance is the derived T * 4u per
+amplitude (u = 2^-24), relative to the 2-norm of the window's initial state,
+which bounds every amplitude the unitary walk can produce inside it.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1003_3779_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def qw():
+    import paper_1003_3779_gb300.qw as qw
+    qw.lib()
+    return qw
+
+
+def test_cycle_2e27_T4096_sweep_sampled(qw):
+    """N = 2^27, SU(2) theta = pi/4, T = 4096, FP32, the random complex64 state of
+    the benchmark, swept at k = 384 with 32 sites per lane (as the benchmark's
+    autotuner picks): eight sampled sites against the oracle, plus the norm."""
+    import torch
+    N, T = 1 << 27, 4096
+    C = inputs.su2(np.pi / 4)
+    psi0 = inputs.random_state((2, N), seed=1, dtype=np.complex64)
+    w = qw.Walk((N,), prec="f32").set_coin(C).set_plan_ex(384, 32, 1)
+    w.set_state(torch.from_numpy(psi0).cuda())
+    w.step(T)
+    assert abs(w.norm() - 1) < T * 4 * U32
+    got = w.state(dtype=np.complex64)
+    rng = np.random.default_rng(7)
+    sample = [0, N - 1, N // 2, 12345] + list(rng.integers(0, N, size=4))
+    for x in sample:
+        idx = (x - T + np.arange(2 * T + 1)) % N
+        win = psi0[:, idx].astype(np.complex128)
+        want = oracle.evolve(win, C, T, bc=oracle.BC_LINE)[:, T]
+        scale = float(np.sqrt((np.abs(win) ** 2).sum()))
+        err = float(np.abs(got[:, x].astype(np.complex128) - want).max())
+        assert err <= T * 4 * U32 * scale, (x, err, scale)
+    w.close()
+
+
+@pytest.mark.parametrize("coin,shift", [("grover", 0), ("hh", 0), ("grover", 1)])
+def test_torus_8192_streaming_sampled(qw, coin, shift):
+    """8192 x 8192 torus, FP32, the streaming kernel at k = 8 as the benchmark
+    times it, T = 64 (eight launches), a random state: sampled sites (corners,
+    edges, interior) against the oracle on their (2T + 1)^2 windows."""
+    import torch
+    L, T = 8192, 64
+    C = {"grover": inputs.grover(), "hh": inputs.hadamard2()}[coin]
+    psi0 = inputs.random_state((4, L, L), seed=2, dtype=np.complex64)
+    w = qw.Walk((L, L), prec="f32", shift=shift).set_coin(C).set_plan(8)
+    assert w.describe()["path"] == "k_step2d_tb"
+    w.set_state(torch.from_numpy(psi0).cuda())
+    w.step(T)
+    got = w.state(dtype=np.complex64)
+    rng = np.random.default_rng(8)
+    sample = [(0, 0), (L - 1, L - 1), (0, L - 1), (L // 2, 47)] + [tuple(p) for p in rng.integers(0, L, size=(3, 2))]
+    M = 2 * T + 1
+    for (x, y) in sample:
+        ix = (x - T + np.arange(M)) % L
+        iy = (y - T + np.arange(M)) % L
+        win = psi0[:, iy][:, :, ix].astype(np.complex128)
+        want = oracle.evolve(win, C, T, shift=shift, bc=oracle.BC_LINE)[:, T, T]
+        scale = float(np.sqrt((np.abs(win) ** 2).sum()))
+        err = float(np.abs(got[:, y, x].astype(np.complex128) - want).max())
+        assert err <= T * 4 * U32 * scale, (x, y, err, scale)
+    w.close()
