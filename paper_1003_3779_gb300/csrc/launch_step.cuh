@@ -94,9 +94,12 @@ template <> struct SweepTiles<P_COMP> { static constexpr int A = 0, B = 0; };
 template <int P>
 int sweep_tile(int64_t n, int tile) {
     using T = SweepTiles<P>;
-    if (T::A == 0) return 0;
-    if (tile == T::A || tile == T::B) return tile;
-    return n % (32LL * T::B) == 0 ? T::B : T::A;
+    if constexpr (T::A == 0) {
+        return 0;
+    } else {
+        if (tile == T::A || tile == T::B) return tile;
+        return n % (32LL * T::B) == 0 ? T::B : T::A;
+    }
 }
 
 template <int P, int R, int CK, int FF, int ADJ>
