@@ -154,9 +154,10 @@ qw_status qw_get_plan(const qw_walk *w, int *depth_k, int *tile);
  * hands two values per step to the next chunk; no halo except one warm-up
  * chunk per segment).  For variant 1, tile is the sites per lane: 16 or 32 in
  * FP32 / BF16 (chunks of 512 or 1024 sites), 8 in FP64 (256 sites); 0 picks
- * the larger tile when N is a multiple of its chunk.  Variant 1 needs the
- * periodic cycle, N a multiple of the chunk, a global coin, FP32 / BF16 /
- * FP64 and k < chunk / 2, else QW_EINVAL.  qw_set_plan selects variant 0. */
+ * the larger tile when the cycle holds two of its chunks.  Variant 1 needs the
+ * periodic cycle, N at least one chunk (any N: the last chunk wraps round), a
+ * global coin, FP32 / BF16 / FP64 and k < chunk / 2, else QW_EINVAL.
+ * qw_set_plan selects variant 0. */
 qw_status qw_set_plan_ex(qw_walk *w, int depth_k, int tile, int variant);
 qw_status qw_get_plan_ex(const qw_walk *w, int *depth_k, int *tile, int *variant);
 

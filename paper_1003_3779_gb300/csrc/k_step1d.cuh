@@ -356,12 +356,19 @@ k_step1d_k1(View in, View out, int64_t n, int64_t nwarps, CoinP<typename St<P>::
 // chunk whose own left edge starts as zeros; its error front moves two sites
 // per step, so k < 16R keeps the handed-over values exact).  The next chunk is
 // prefetched with cp.async into a swizzled shared buffer while the current one
-// computes; each lane then reads its own run conflict-free.
+// computes; each lane then reads its own run conflict-free.  Any n >= 32R: the
+// last chunk may reach past site n - 1 and wrap.
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// One site's slot (4, 8 or 16 bytes), both addresses aligned to its size.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_slot(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Lane 31 stores (v2, v1) at eout and loads (v2, v1) from ein; the other lanes
@@ -425,18 +432,35 @@ k_step1d_sweep(View in, View out, int64_t n, int K, int nch, int64_t nseg, CoinP
     uint4 *cbuf = reinterpret_cast<uint4 *>(wbase);
     C *edge = reinterpret_cast<C *>(wbase + SW::chunk_bytes);
     const int64_t s0 = seg * (int64_t)nch * B;
-    const int nchs = (int)min((int64_t)nch, (n - s0) / B);
+    // the last chunk of the cycle may run past site n - 1: it wraps to the first
+    // sites, which it recomputes (with their true left context) to the same bits
+    const int nchs = (int)min((int64_t)nch, (n - s0 + B - 1) / B);
 
     auto prefetch = [&](int j) {
         int64_t start = s0 + (int64_t)j * B;
         if (start < 0) start += n;
+        if (start + B <= n && start % VEC == 0) {   // a contiguous, 16-byte aligned run
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const char *g = static_cast<const char *>(in.p) + (c * in.pitch + start) * S::SLOT_BYTES;
+            for (int c = 0; c < 2; ++c) {
+                const char *g = static_cast<const char *>(in.p) + (c * in.pitch + start) * S::SLOT_BYTES;
 #pragma unroll
-            for (int i = 0; i < CPL; ++i) {
-                const int u = i * 32 + lane;
-                cp_async16(cbuf + c * 32 * CPL + swz<CPL>(u / CPL, u % CPL), g + (size_t)u * 16);
+                for (int i = 0; i < CPL; ++i) {
+                    const int u = i * 32 + lane;
+                    cp_async16(cbuf + c * 32 * CPL + swz<CPL>(u / CPL, u % CPL), g + (size_t)u * 16);
+                }
+            }
+        } else {   // across site n - 1 (or after it, unaligned): this lane's own sites one by one
+            // (rolled loops: the rare path must not cost the main loop registers)
+            constexpr int UPV = 16 / S::SLOT_BYTES;
+#pragma unroll 1
+            for (int c = 0; c < 2; ++c) {
+#pragma unroll 1
+                for (int i = 0; i < R; ++i) {
+                    const int64_t g = (start + (int64_t)lane * R + i) % n;
+                    void *dst = reinterpret_cast<unsigned char *>(cbuf + c * 32 * CPL + swz<CPL>(lane, i / UPV)) +
+                                (i % UPV) * S::SLOT_BYTES;
+                    cp_async_slot<S::SLOT_BYTES>(dst, static_cast<const char *>(in.p) + (c * in.pitch + g) * S::SLOT_BYTES);
+                }
             }
         }
         cp_async_commit();

@@ -89,8 +89,8 @@ template <> struct SweepTiles<P_F64> { static constexpr int A = 8, B = 8; };
 template <> struct SweepTiles<P_COMP> { static constexpr int A = 0, B = 0; };
 
 // The sites per lane a sweep plan with this tile runs on a cycle of n sites:
-// the requested tile if it is compiled, else the larger tile when n is a
-// multiple of its chunk, else the smaller one.
+// the requested tile if it is compiled, else the larger tile when the cycle
+// holds at least two of its chunks, else the smaller one.
 template <int P>
 int sweep_tile(int64_t n, int tile) {
     using T = SweepTiles<P>;
@@ -98,7 +98,7 @@ int sweep_tile(int64_t n, int tile) {
         return 0;
     } else {
         if (tile == T::A || tile == T::B) return tile;
-        return n % (32LL * T::B) == 0 ? T::B : T::A;
+        return n >= 2 * 32LL * T::B ? T::B : T::A;
     }
 }
 
@@ -121,10 +121,10 @@ static cudaError_t go1d_sweep(const Step1DArgs &a, const CoinP<typename St<P>::r
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * warps, smem);
         const int64_t resident = (int64_t)std::max(1, sms) * std::max(1, per_sm) * warps;
-        const int64_t chunks = a.n / SW::B;
+        const int64_t chunks = (a.n + SW::B - 1) / SW::B;
         nch = (int)std::max<int64_t>(1, (chunks + resident - 1) / resident);
     }
-    const int64_t nseg = (a.n / SW::B + nch - 1) / nch;
+    const int64_t nseg = ((a.n + SW::B - 1) / SW::B + nch - 1) / nch;
     const int64_t blocks = (nseg + warps - 1) / warps;
     kfn<<<(unsigned)blocks, 32 * warps, smem, s>>>(a.in, a.out, a.n, a.K, nch, nseg, cp,
                                                   real_from_double<real>(a.pre0), real_from_double<real>(a.pre1),
@@ -144,13 +144,13 @@ static cudaError_t go1d_sweep_kind(const Step1DArgs &a, const CoinP<typename St<
     }
 }
 
-// Can the sweep kernel run this launch?  (n a multiple of the chunk of the
-// tile sweep_tile picks, 2 <= K < chunk / 2.)
+// Can the sweep kernel run this launch?  (n at least the chunk of the tile
+// sweep_tile picks, 2 <= K < chunk / 2.)
 template <int P>
 bool sweep_ok(int64_t n, int K, int kind, int tile) {
     if (P == P_COMP || kind == CK_PERSITE || kind == CK_PHASE) return false;
     const int64_t B = 32LL * sweep_tile<P>(n, tile);
-    return B > 0 && n % B == 0 && n >= B && K >= 2 && K <= B / 2 - 1;
+    return B > 0 && n >= B && K >= 2 && K <= B / 2 - 1;
 }
 
 // Largest K the 1D kernel accepts for tile R: at least half the tile is output.

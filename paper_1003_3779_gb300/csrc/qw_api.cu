@@ -718,7 +718,7 @@ qw_status qw_set_plan_ex(qw_walk *w, int depth_k, int tile, int variant) {
         return st;
     }
     if (w->ndim != 1 || depth_k < 1 || !sweep_ok(w, std::max(depth_k, 2), tile))
-        return set_error(w, QW_EINVAL, "the sweep kernel needs the periodic 1D walk, N a multiple of its "
+        return set_error(w, QW_EINVAL, "the sweep kernel needs the periodic 1D walk, N at least its "
                                        "chunk (32 x tile sites), a global coin, FP32/BF16/FP64 and "
                                        "1 <= k < chunk / 2");
     w->plan_k = depth_k; w->plan_tile = sweep_tile(w, tile); w->plan_variant = 1;

@@ -223,6 +223,9 @@ def test_hadamard_class_coins(qw, prec, m00, m01, m10):
 
 def test_describe_reports_the_kernel_path(qw):
     w = qw.Walk((1000,), prec="f32").set_coin(inputs.su2(np.pi / 4))
+    assert w.describe()["path"] == "k_step1d_sweep"      # at least one 512-site chunk
+    w.close()
+    w = qw.Walk((300,), prec="f32").set_coin(inputs.su2(np.pi / 4))
     d = w.describe()
     assert d["coin_kind"] == "hadamard_class" and d["path"] == "k_step1d"
     w.set_coin(inputs.su2(0.3))
@@ -248,9 +251,12 @@ def test_norm_drift_compensated_long_run(qw, theta):
 
 
 # (precision, N, sites per lane): both compiled tiles of the float forms (chunks
-# of 512 and 1024 sites), several segments with a short last one, one-chunk cycles
+# of 512 and 1024 sites), several segments with a short last one, one-chunk cycles,
+# and cycles whose last chunk runs past site N - 1 (odd N too)
 SWEEP_CASES = [("f32", 512 * 37, 16), ("f32", 512, 16), ("f32", 1024 * 19, 32), ("f32", 1024, 32),
-               ("bf16", 512 * 21, 16), ("bf16", 1024 * 11, 32), ("f64", 256 * 35, 8)]
+               ("f32", 1024 * 19 + 333, 32), ("f32", 512 * 3 + 1, 16), ("f32", 1024 + 7, 32),
+               ("bf16", 512 * 21, 16), ("bf16", 1024 * 11, 32), ("bf16", 1024 * 11 + 3, 32),
+               ("f64", 256 * 35, 8), ("f64", 256 * 35 + 101, 8)]
 SWEEP_COINS = {"hadamard_class": inputs.su2(np.pi / 4), "real": inputs.su2(0.3),
                "complex": inputs.su2(0.3, 0.2, -0.5)}
 
@@ -293,7 +299,7 @@ def test_sweep_kernel_deep(qw, prec, N, tile, k, coin, adj):
 
 
 def test_sweep_default_tile_follows_the_cycle_length(qw):
-    for N, tile in ((1024 * 5, 32), (512 * 5, 16)):
+    for N, tile in ((1024 * 5, 32), (2048, 32), (2047, 16), (700, 16)):
         w = qw.Walk((N,), prec="f32").set_coin(inputs.hadamard())
         w.set_plan_ex(64, 0, 1)
         assert w.plan_ex() == (64, tile, 1)
@@ -301,13 +307,13 @@ def test_sweep_default_tile_follows_the_cycle_length(qw):
 
 
 def test_sweep_rejected_where_it_cannot_run(qw):
+    w = qw.Walk((500,), prec="f32").set_coin(inputs.hadamard())
+    with pytest.raises(qw.QWError):
+        w.set_plan_ex(16, 0, 1)          # 500 sites are less than one 512-site chunk
+    w.close()
     w = qw.Walk((1000,), prec="f32").set_coin(inputs.hadamard())
     with pytest.raises(qw.QWError):
-        w.set_plan_ex(16, 0, 1)          # 1000 is not a multiple of 512
-    w.close()
-    w = qw.Walk((512 * 3,), prec="f32").set_coin(inputs.hadamard())
-    with pytest.raises(qw.QWError):
-        w.set_plan_ex(16, 32, 1)         # 1536 is not a multiple of the 1024-site chunk
+        w.set_plan_ex(16, 32, 1)         # ... or one 1024-site chunk
     with pytest.raises(qw.QWError):
         w.set_plan_ex(256, 16, 1)        # k must stay below half the 512-site chunk
     w.close()
