@@ -61,6 +61,10 @@ def _lib(openmp: bool = False):
             lib.oracle_region_grad.argtypes = [P, ctypes.c_int, P, P, P, ctypes.c_int64,
                                                P, P, P]
             lib.oracle_num_threads.argtypes = []
+            lib.oracle_philox4x32_10.argtypes = [P, P, P]
+            lib.oracle_philox4x32_10.restype = None
+            lib.oracle_link_masks.argtypes = [ctypes.c_int, P, ctypes.c_uint64, ctypes.c_uint32,
+                                              ctypes.c_int64, ctypes.c_int64, P]
             _LIBS[openmp] = lib
         return _LIBS[openmp]
 
@@ -124,6 +128,34 @@ def evolve(psi, coin, T, *, shift=SHIFT_MOVING, bc=BC_PERIODIC, coin_mode=None,
                                     _ptr(coin), _ptr(phi_a), _ptr(psi), int(T),
                                     int(bool(adjoint)), _ptr(out))
     _check(st, "oracle_evolve")
+    return out
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32 with 10 rounds (Salmon et al., SC 2011): four 32-bit words."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.empty(4, dtype=np.uint32)
+    _lib().oracle_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def link_threshold(p):
+    """The 32-bit threshold of closing probability p (a link closes when a
+    Philox word is below it)."""
+    return min(int(p * 4294967296.0), 4294967295)
+
+
+def link_masks(plane_shape, seed, p, t0, T):
+    """Closed-link masks of steps t0 .. t0+T-1 (Sec. 3, links broken at random at
+    every step): uint8 array (T, ndim, nsites) for evolve(..., closed_per_step=True)."""
+    shape = tuple(int(x) for x in plane_shape)
+    ndim = len(shape)
+    dims = np.array(shape[::-1], dtype=np.int64)   # (nx,) or (nx, ny)
+    ns = int(np.prod(shape))
+    out = np.empty((int(T), ndim, ns), dtype=np.uint8)
+    st = _lib().oracle_link_masks(ndim, _ptr(dims), int(seed), link_threshold(p), int(t0), int(T), _ptr(out))
+    _check(st, "oracle_link_masks")
     return out
 
 

@@ -343,6 +343,56 @@ int oracle_region_grad(const int64_t *dims, int shift, const double *base,
 }
 
 /* Number of threads the OpenMP build runs with (1 without OpenMP). */
+/* ---------------------------------------------------------------------------
+ * Random broken links resampled at every step (Sec. 3: the RBL function, a
+ * link that breaks at random).  The randomness is a counter-based generator,
+ * Philox4x32 with 10 rounds (Salmon, Moraes, Dror and Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3", SC 2011), written here from that definition:
+ * a round maps the counter (c0, c1, c2, c3) with the key (k0, k1) to
+ * (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)), where hi
+ * and lo are the halves of the 64-bit products with M0 = 0xD2511F53 and
+ * M1 = 0xCD9E8D57, and the key grows by (0x9E3779B9, 0xBB67AE85) before every
+ * round after the first.
+ *
+ * Link (axis, site) is closed at step t when word 0 of Philox(counter =
+ * (site low 32 bits, site high 32 bits, t, axis), key = (seed low, seed high))
+ * is below the threshold (the closing probability times 2^32).
+ */
+void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* The closed-link masks of steps t0 .. t0+T-1: out holds T masks of ndim*nsites
+ * flags in the layout oracle_evolve takes (x-links, then y-links). */
+int oracle_link_masks(int ndim, const int64_t *dims, uint64_t seed, uint32_t threshold,
+                      int64_t t0, int64_t T, uint8_t *out)
+{
+    if ((ndim != 1 && ndim != 2) || !dims || T < 0 || !out) return OR_EINVAL;
+    int64_t ns = dims[0] * (ndim == 2 ? dims[1] : 1);
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int64_t t = 0; t < T; ++t)
+        for (int axis = 0; axis < ndim; ++axis)
+            for (int64_t v = 0; v < ns; ++v) {
+                uint32_t ctr[4] = {(uint32_t)v, (uint32_t)((uint64_t)v >> 32), (uint32_t)(t0 + t), (uint32_t)axis};
+                uint32_t r[4];
+                oracle_philox4x32_10(ctr, key, r);
+                out[((size_t)t * ndim + axis) * ns + v] = r[0] < threshold;
+            }
+    return OR_OK;
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP

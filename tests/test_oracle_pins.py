@@ -8,6 +8,7 @@ reflection slot or a wrong adjoint each fail at least one test (see
 ``test_planted_mistakes_are_caught``).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -176,6 +177,37 @@ def test_dense_closed_per_step():
     assert np.abs(got.reshape(-1) - want).max() < 1e-12
     back = oracle.evolve(got, C, T, closed=masks, closed_per_step=True, adjoint=True)
     assert np.abs(back - psi0).max() < 1e-12
+
+
+# ------------------------------------------------------------ links broken at random each step
+def test_philox_known_answers():
+    """The oracle's Philox4x32-10 reproduces the generator's published
+    known-answer vectors (tests/golden/philox4x32_10_kat.txt)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        got = oracle.philox4x32_10(v[0:4], v[4:6])
+        assert list(got) == v[6:10]
+
+
+def test_link_masks_rate_and_independence():
+    """Per-step masks: each link closes with probability p (binomial bound), the
+    masks of different steps, axes and seeds differ, and the same (seed, step)
+    gives the same mask."""
+    p, shape = 0.3, (40, 50)
+    m = oracle.link_masks(shape, seed=12345, p=p, t0=7, T=6)
+    assert m.shape == (6, 2, 2000)
+    n = m.size
+    assert abs(m.mean() - p) < 5 * np.sqrt(p * (1 - p) / n)
+    assert not np.array_equal(m[0], m[1]) and not np.array_equal(m[0, 0], m[0, 1])
+    again = oracle.link_masks(shape, seed=12345, p=p, t0=8, T=1)
+    assert np.array_equal(again[0], m[1])
+    other = oracle.link_masks(shape, seed=12346, p=p, t0=7, T=1)
+    assert not np.array_equal(other[0], m[0])
+    assert oracle.link_masks(shape, seed=1, p=0.0, t0=0, T=2).sum() == 0
+    assert oracle.link_masks(shape, seed=1, p=1.0, t0=0, T=1).all()
 
 
 # ------------------------------------------------------------ invariants
