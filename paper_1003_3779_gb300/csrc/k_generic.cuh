@@ -19,7 +19,26 @@ struct GenGeom {
     int64_t nx, ny, ns;
     int shift, bc;
     const uint8_t *links;
+    uint32_t rthr, rk0, rk1, rstep;   // links broken at random at this step (rthr 0: none)
 };
+
+// Word 0 of Philox4x32 with 10 rounds (Salmon, Moraes, Dror and Shaw, SC 2011)
+// for counter (c0, c1, c2, c3) and key (k0, k1): each round multiplies c0 and
+// c2 by 0xD2511F53 and 0xCD9E8D57 and mixes the product halves with c1, c3 and
+// the key, which then grows by (0x9E3779B9, 0xBB67AE85).
+__device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                 uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t h0 = __umulhi(0xD2511F53u, c0), l0 = 0xD2511F53u * c0;
+        const uint32_t h1 = __umulhi(0xCD9E8D57u, c2), l1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = h1 ^ c1 ^ k0, n2 = h0 ^ c3 ^ k1;
+        c0 = n0; c1 = l1; c2 = n2; c3 = l0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c0;
+}
 
 // Axis and sign of coin c: 1D coin 0 -> -x, coin 1 -> +x; 2D 0 +x, 1 -x, 2 +y, 3 -y.
 __device__ __forceinline__ void coin_dir(int ndim, int c, int &axis, int &sgn) {
@@ -38,9 +57,11 @@ __device__ __forceinline__ int move_along(const GenGeom &g, int64_t x, int64_t y
     const int64_t lp = sgn > 0 ? p : (p == 0 ? n - 1 : p - 1);   // link (lp, lp+1)
     const bool edge = (lp == n - 1);
     bool closed = false;
-    if (g.links) {
-        const int64_t lx = axis == 0 ? lp : x, ly = axis == 0 ? y : lp;
-        closed = g.links[axis * g.ns + ly * g.nx + lx] != 0;
+    const int64_t lx = axis == 0 ? lp : x, ly = axis == 0 ? y : lp;
+    if (g.links) closed = g.links[axis * g.ns + ly * g.nx + lx] != 0;
+    if (!closed && g.rthr) {   // broken at random at this step (Sec. 3, the RBL function)
+        const uint64_t v = (uint64_t)(ly * g.nx + lx);
+        closed = philox_word0((uint32_t)v, (uint32_t)(v >> 32), g.rstep, (uint32_t)axis, g.rk0, g.rk1) < g.rthr;
     }
     if (edge && g.bc == QW_BC_SEGMENT) closed = true;
     int64_t q = p + sgn;

@@ -249,7 +249,7 @@ cudaError_t step2d_t(const Step2DArgs &a, const void *coinp, int adj, cudaStream
 
 template <int P, int CK>
 static void gogen(const StepGenericArgs &a, const CoinP<typename St<P>::real> &cp, cudaStream_t s) {
-    GenGeom g{a.ndim, a.nx, a.ny, a.nx * a.ny, a.shift, a.bc, a.links};
+    GenGeom g{a.ndim, a.nx, a.ny, a.nx * a.ny, a.shift, a.bc, a.links, a.rthr, a.rk0, a.rk1, a.rstep};
     const int64_t blocks = (g.ns + 127) / 128;
     k_step_generic<P, CK><<<(unsigned)blocks, 128, 0, s>>>(
         a.in, a.out, g, a.adjoint, cp, static_cast<const Cx<typename St<P>::real> *>(a.coins), a.phi,

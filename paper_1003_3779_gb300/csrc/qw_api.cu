@@ -96,7 +96,7 @@ static int tile1d(int prec, int tile, int kind, int adj) {
 // Sweep plans: `tile` is the sites per lane (0 or an uncompiled value: the
 // launcher's default for this cycle length).
 static bool sweep_ok(const qw_walk *w, int K, int tile) {
-    if (w->ndim != 1 || w->bc != QW_BC_PERIODIC || w->has_links) return false;
+    if (w->ndim != 1 || w->bc != QW_BC_PERIODIC || links_on(w)) return false;
     switch (w->prec) {
         case QW_F64: return sweep_ok_f64(w->nx, K, w->kind, tile);
         case QW_F32: return sweep_ok_f32(w->nx, K, w->kind, tile);
@@ -133,7 +133,7 @@ static void default_plan(const qw_walk *w, int &k, int &tile, int &variant) {
         // (8 per SM), else the fused single step
         tile = 0;
         k = 1;
-        if (w->bc != QW_BC_PERIODIC || w->has_links) return;
+        if (w->bc != QW_BC_PERIODIC || links_on(w)) return;
         static int sms = 0;
         if (!sms) {
             int dev = 0;
@@ -311,7 +311,7 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
     if (T < 0) return set_error(w, QW_EINVAL, "T must be >= 0");
     if (T == 0) return QW_OK;
     const void *cp = w->coinp;
-    bool generic = w->bc != QW_BC_PERIODIC || w->has_links;
+    bool generic = w->bc != QW_BC_PERIODIC || links_on(w);
     if (!generic && w->ndim == 2) {
         if (w->kind == CK_PERSITE) generic = true;
         if (w->kind == CK_PHASE && !(w->prec == QW_F32 || w->prec == QW_F64)) generic = true;
@@ -322,8 +322,15 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
         a.ndim = w->ndim; a.nx = w->nx; a.ny = w->ny; a.shift = w->shift; a.bc = w->bc;
         a.kind = w->kind; a.coins = w->coins_dev; a.phi = w->phi_dev;
         a.links = w->has_links ? w->links_dev : nullptr; a.adjoint = adj;
+        a.rthr = w->link_thr;
+        a.rk0 = (uint32_t)w->link_seed; a.rk1 = (uint32_t)(w->link_seed >> 32);
         if (w->kind == CK_SIGN_P || w->kind == CK_SIGN_M) a.kind = CK_COMPLEX;   // generic reads the matrix
         for (int64_t t = 0; t < T; ++t) {
+            // random links: a forward step draws the mask of its index, then counts
+            // up; the adjoint counts down first, so it undoes the last forward step
+            if (w->link_thr && adj) --w->link_step;
+            a.rstep = (uint32_t)w->link_step;
+            if (w->link_thr && !adj) ++w->link_step;
             a.gain = drift_gain(w, 1, t + 1 == T);
             a.in = cur_view(w); a.out = next_view(w);
             if ((e = stepgen(w->prec, a, cp, w->stream)) != cudaSuccess) return cuda_error(w, e, "generic step launch");
@@ -565,6 +572,24 @@ qw_status qw_set_links(qw_walk *w, const uint8_t *closed, int on_device) {
     return QW_OK;
 }
 
+qw_status qw_set_link_noise(qw_walk *w, double p, uint64_t seed, int64_t step) {
+    if (!w) return QW_EINVAL;
+    if (!(p >= 0.0 && p <= 1.0)) return set_error(w, QW_EINVAL, "p must be in [0, 1]");
+    if (p > 0.0 && w->shift == QW_SHIFT_DIAGONAL)
+        return set_error(w, QW_EUNSUPPORTED, "broken links are defined on the axis lattice");
+    const double scaled = p * 4294967296.0;
+    w->link_thr = scaled >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)scaled;
+    w->link_seed = seed;
+    w->link_step = step;
+    return QW_OK;
+}
+
+qw_status qw_get_link_step(const qw_walk *w, int64_t *step) {
+    if (!w || !step) return QW_EINVAL;
+    *step = w->link_step;
+    return QW_OK;
+}
+
 static bool direct_layout(const qw_walk *w, qw_cdtype dt) {
     return (w->prec == QW_F32 && dt == QW_C64) || (w->prec == QW_F64 && dt == QW_C128);
 }
@@ -742,7 +767,7 @@ qw_status qw_describe(const qw_walk *w, char *buf, size_t len) {
     int k, t, var;
     effective_plan(w, k, t, var);
     if (w->ndim == 1) t = var == 1 ? sweep_tile(w, t) : tile1d(w->prec, t, w->kind, 0);
-    const bool generic = w->bc != QW_BC_PERIODIC || w->has_links ||
+    const bool generic = w->bc != QW_BC_PERIODIC || links_on(w) ||
                          (w->ndim == 2 && (w->kind == CK_PERSITE ||
                                            (w->kind == CK_PHASE && !(w->prec == QW_F32 || w->prec == QW_F64))));
     std::snprintf(buf, len,
@@ -821,7 +846,7 @@ extern "C" qw_status qw_autotune(qw_walk *w, char *report, size_t report_len) {
     auto put = [&](const char *s) {
         if (report && report_len) { std::strncpy(report, s, report_len - 1); report[report_len - 1] = 0; }
     };
-    if (w->bc != QW_BC_PERIODIC || w->has_links) {
+    if (w->bc != QW_BC_PERIODIC || links_on(w)) {
         put("{\"tuned\": false, \"reason\": \"the generic boundary / broken-link kernel has no plan space\"}");
         return QW_OK;
     }

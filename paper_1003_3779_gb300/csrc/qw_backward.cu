@@ -177,7 +177,7 @@ extern "C" qw_status qw_backward(qw_walk *w, const int64_t rect[4], int64_t T, i
     if (w->ndim != 2) return set_error(w, QW_EUNSUPPORTED, "qw_backward is defined on the torus");
     if (w->kind != CK_PHASE) return set_error(w, QW_ESTATE, "qw_backward needs a phase coin (qw_set_coin_phases)");
     if (w->prec != QW_F32 && w->prec != QW_F64) return set_error(w, QW_EUNSUPPORTED, "qw_backward runs in FP32 or FP64");
-    if (w->bc != QW_BC_PERIODIC || w->has_links) return set_error(w, QW_EUNSUPPORTED, "qw_backward needs the periodic torus");
+    if (w->bc != QW_BC_PERIODIC || links_on(w)) return set_error(w, QW_EUNSUPPORTED, "qw_backward needs the periodic torus");
     if (rect[0] < 0 || rect[1] < 0 || rect[2] < 0 || rect[3] < 0 || rect[0] + rect[2] > w->nx || rect[1] + rect[3] > w->ny)
         return set_error(w, QW_EINVAL, "rect outside the lattice");
 

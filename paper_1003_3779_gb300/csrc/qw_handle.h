@@ -37,6 +37,11 @@ struct qw_walk {
     float *phi_dev = nullptr;              // per-site phases, nsites * d
     uint8_t *links_dev = nullptr;          // closed-link flags, ndim * nsites
     bool has_links = false;
+    // links broken at random at every step (qw_set_link_noise): Philox threshold
+    // (0: off), key, and the index of the next forward step
+    uint32_t link_thr = 0;
+    uint64_t link_seed = 0;
+    int64_t link_step = 0;
 
     // reductions
     double *partials = nullptr;
@@ -72,6 +77,8 @@ inline View view_of(const qw_walk *w, int which) {
     return View{w->buf[which], w->pitch, w->d};
 }
 inline View cur_view(const qw_walk *w) { return view_of(w, w->cur); }
+// any closed links, fixed or broken at random: the generic kernel then runs
+inline bool links_on(const qw_walk *w) { return w->has_links || w->link_thr != 0; }
 inline View next_view(const qw_walk *w) { return view_of(w, w->cur ^ 1); }
 
 // Runs T steps of U (adj = 0) or U^dagger (adj = 1) from buffer `src` into

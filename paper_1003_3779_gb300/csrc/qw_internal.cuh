@@ -370,6 +370,9 @@ struct StepGenericArgs {
     const uint8_t *links;
     int adjoint;
     double gain;         // factor applied to every step's output
+    // links broken at random: closed when Philox word 0 < rthr (0: off), key
+    // (rk0, rk1), step index rstep
+    uint32_t rthr, rk0, rk1, rstep;
 };
 cudaError_t launch_step_generic(int prec, const StepGenericArgs &a, const void *coinp, cudaStream_t s);
 

@@ -53,6 +53,8 @@ def lib():
         "qw_set_coin": (I, [P, P, I, I]),
         "qw_set_coin_phases": (I, [P, P, P, I]),
         "qw_set_links": (I, [P, P, I]),
+        "qw_set_link_noise": (I, [P, ctypes.c_double, ctypes.c_uint64, I64]),
+        "qw_get_link_step": (I, [P, P]),
         "qw_set_state": (I, [P, P, I, I]),
         "qw_get_state": (I, [P, P, I, I]),
         "qw_step": (I, [P, I64]),
@@ -165,6 +167,16 @@ def qw_set_links(h, closed):
     if isinstance(closed, np.ndarray):
         closed = np.ascontiguousarray(closed, dtype=np.uint8)
     _check(lib().qw_set_links(h, _ptr(closed), _on_device(closed) if closed is not None else 0), h)
+
+
+def qw_set_link_noise(h, p, seed, step=0):
+    _check(lib().qw_set_link_noise(h, float(p), int(seed) & 0xFFFFFFFFFFFFFFFF, int(step)), h)
+
+
+def qw_get_link_step(h):
+    t = ctypes.c_int64(0)
+    _check(lib().qw_get_link_step(h, ctypes.byref(t)), h)
+    return t.value
 
 
 def _cdtype(x):
@@ -316,6 +328,14 @@ class Walk:
     def set_links(self, closed):
         qw_set_links(self.h, closed)
         return self
+
+    def set_link_noise(self, p, seed, step=0):
+        """Links broken at random afresh at every step with probability p."""
+        qw_set_link_noise(self.h, p, seed, step)
+        return self
+
+    def link_step(self):
+        return qw_get_link_step(self.h)
 
     def set_state(self, amp):
         qw_set_state(self.h, amp)
