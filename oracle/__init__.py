@@ -65,6 +65,10 @@ def _lib(openmp: bool = False):
             lib.oracle_philox4x32_10.restype = None
             lib.oracle_link_masks.argtypes = [ctypes.c_int, P, ctypes.c_uint64, ctypes.c_uint32,
                                               ctypes.c_int64, ctypes.c_int64, P]
+            lib.oracle_graph_arcs.argtypes = [ctypes.c_int64, ctypes.c_int64, P, P, P]
+            lib.oracle_graph_evolve.argtypes = [ctypes.c_int64, P, P, ctypes.c_int, P, P,
+                                                ctypes.c_int64, ctypes.c_int, P]
+            lib.oracle_graph_probabilities.argtypes = [ctypes.c_int64, P, P, P, P]
             _LIBS[openmp] = lib
         return _LIBS[openmp]
 
@@ -190,3 +194,61 @@ def region_grad(psi0, base, phi, T, rect, *, shift=SHIFT_MOVING, openmp=False):
                                          _ptr(grad))
     _check(st, "oracle_region_grad")
     return loss.value, grad.reshape(int(dims[1]), int(dims[0]), 4)
+
+
+GRAPH_COIN_GROVER, GRAPH_COIN_PER_VERTEX = 0, 1
+
+
+def graph_arcs(nvert, edges):
+    """Arc form (off, partner) of a graph given as an edge list (Sec. 2.1): the
+    arcs of vertex v are off[v] .. off[v+1]-1, in the order the vertex's edge
+    ends appear in the list; partner[a] is the arc at the other end of a's edge."""
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int64).reshape(-1, 2))
+    off = np.empty(int(nvert) + 1, dtype=np.int64)
+    partner = np.empty(2 * len(e), dtype=np.int64)
+    st = _lib().oracle_graph_arcs(int(nvert), len(e), _ptr(e), _ptr(off), _ptr(partner))
+    _check(st, "oracle_graph_arcs")
+    return off, partner
+
+
+def graph_evolve(off, partner, psi, T, *, coins=None, adjoint=False, openmp=False):
+    """U^T psi (or (U^dagger)^T psi) for the walk on a general graph in arc form
+    (Sec. 2.1, U = S (I (x) C), S|v,e> = |v',e>).  coins None: the Grover coin
+    (2/d) J - I at every vertex; else a list of per-vertex d(v) x d(v) matrices,
+    or one d x d matrix for a d-regular graph."""
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    partner = np.ascontiguousarray(partner, dtype=np.int64)
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    nvert = len(off) - 1
+    if psi.shape != (int(off[-1]),):
+        raise ValueError("psi must hold one amplitude per arc")
+    mode, flat = GRAPH_COIN_GROVER, None
+    if coins is not None:
+        mode = GRAPH_COIN_PER_VERTEX
+        deg = np.diff(off)
+        if isinstance(coins, np.ndarray) and coins.ndim == 2:
+            if np.any(deg != coins.shape[0]):
+                raise ValueError("one matrix for all vertices needs a regular graph of that degree")
+            flat = np.ascontiguousarray(np.tile(coins.astype(np.complex128).ravel(), nvert))
+        else:
+            parts = [np.asarray(c, dtype=np.complex128).ravel() for c in coins]
+            if len(parts) != nvert or any(p.size != d * d for p, d in zip(parts, deg)):
+                raise ValueError("one d(v) x d(v) matrix per vertex")
+            flat = np.ascontiguousarray(np.concatenate(parts) if parts else np.zeros(0, complex))
+    out = np.empty_like(psi)
+    st = _lib(openmp).oracle_graph_evolve(nvert, _ptr(off), _ptr(partner), mode, _ptr(flat),
+                                          _ptr(psi), int(T), int(bool(adjoint)), _ptr(out))
+    _check(st, "oracle_graph_evolve")
+    return out
+
+
+def graph_probabilities(off, psi):
+    """Return (P, norm): P(v) = sum over the arcs of v of |psi(a)|^2."""
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    P = np.empty(len(off) - 1, dtype=np.float64)
+    norm = ctypes.c_double(0.0)
+    st = _lib().oracle_graph_probabilities(len(off) - 1, _ptr(off), _ptr(psi), _ptr(P),
+                                           ctypes.cast(ctypes.pointer(norm), ctypes.c_void_p))
+    _check(st, "oracle_graph_probabilities")
+    return P, norm.value

@@ -1,7 +1,7 @@
 /*
  * qw_oracle.c -- plain, slow, FP64 CPU oracle for the discrete-time coined
- * quantum walk on the cycle Z_N (coin dim 2) and the torus Z_Lx x Z_Ly
- * (coin dim 4).
+ * quantum walk on the cycle Z_N (coin dim 2), the torus Z_Lx x Z_Ly
+ * (coin dim 4) and a general graph (coin dim = vertex degree, Sec. 2.1).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
  * benchmark's CPU-baseline / reference arm may load this file.  It shares no
@@ -401,4 +401,160 @@ int oracle_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------ graphs
+ * The discrete-time walk on a general graph G = (V, E) (Sec. 2.1).  The local
+ * space of vertex v is spanned by one basis state |v, e> per edge e at v, so
+ * the global space has one basis state per (vertex, edge-end) pair: an "arc".
+ * Arc form used here: the arcs of vertex v are off[v] .. off[v+1]-1 in a fixed
+ * slot order, and partner[a] is the arc |v', e> at the other end of the same
+ * edge e = {v, v'} (a loop contributes two arcs at v, partners of each other).
+ * The shift S|v,e> = |v',e> is then |a> -> |partner[a]>, an involution, and the
+ * coin C_v acts on the d(v) arcs of v.  One step is U = S (I (x) C).
+ *
+ * Coin modes: 0 Grover, C_v = (2/d(v)) J - I on every vertex (the standard coin
+ * of graph walks; J the all-ones matrix); 1 one d(v) x d(v) matrix per vertex,
+ * concatenated in vertex order, row-major, interleaved re/im doubles.
+ */
+
+/* Build the arc form from an edge list (pairs of vertex indices).  Slots of a
+ * vertex follow the order in which its edge ends appear in the list: edge i
+ * = (u, w) gives u the arc of end 0 and w the arc of end 1 (both at u for a
+ * loop, end 0 first).  off: nvert+1 entries; partner: 2*nedges entries. */
+int oracle_graph_arcs(int64_t nvert, int64_t nedges, const int64_t *edges, int64_t *off, int64_t *partner)
+{
+    if (nvert < 1 || nedges < 0 || (nedges && !edges) || !off || (nedges && !partner)) return OR_EINVAL;
+    for (int64_t i = 0; i < 2 * nedges; ++i)
+        if (edges[i] < 0 || edges[i] >= nvert) return OR_EINVAL;
+    int64_t *deg = calloc((size_t)nvert, sizeof(int64_t));
+    int64_t *arc = malloc(sizeof(int64_t) * (size_t)(2 * nedges + 1));
+    if (!deg || !arc) { free(deg); free(arc); return OR_ENOMEM; }
+    /* each edge end, in list order, takes the next free slot of its vertex */
+    for (int64_t i = 0; i < 2 * nedges; ++i) arc[i] = deg[edges[i]]++;
+    off[0] = 0;
+    for (int64_t v = 0; v < nvert; ++v) off[v + 1] = off[v] + deg[v];
+    for (int64_t i = 0; i < 2 * nedges; ++i) arc[i] += off[edges[i]];
+    for (int64_t e = 0; e < nedges; ++e) {
+        partner[arc[2 * e]] = arc[2 * e + 1];
+        partner[arc[2 * e + 1]] = arc[2 * e];
+    }
+    free(deg); free(arc);
+    return OR_OK;
+}
+
+typedef struct {
+    int64_t nvert, narcs;
+    const int64_t *off, *partner;
+    int coin_mode;
+    const cplx *coins;        /* mode 1 */
+    int64_t *coin_at;         /* mode 1: first entry of vertex v's matrix */
+} graph;
+
+static int graph_init(graph *G, int64_t nvert, const int64_t *off, const int64_t *partner,
+                      int coin_mode, const double *coins)
+{
+    if (nvert < 1 || !off || off[0] != 0 || (coin_mode != 0 && coin_mode != 1) || (coin_mode == 1 && !coins))
+        return OR_EINVAL;
+    for (int64_t v = 0; v < nvert; ++v)
+        if (off[v + 1] < off[v]) return OR_EINVAL;
+    G->nvert = nvert;
+    G->narcs = off[nvert];
+    G->off = off;
+    G->partner = partner;
+    G->coin_mode = coin_mode;
+    G->coins = (const cplx *)coins;
+    G->coin_at = NULL;
+    if (G->narcs && !partner) return OR_EINVAL;
+    /* S must be a permutation of the arcs that is its own inverse */
+    for (int64_t a = 0; a < G->narcs; ++a)
+        if (partner[a] < 0 || partner[a] >= G->narcs || partner[partner[a]] != a) return OR_EINVAL;
+    if (coin_mode == 1) {
+        G->coin_at = malloc(sizeof(int64_t) * (size_t)nvert);
+        if (!G->coin_at) return OR_ENOMEM;
+        int64_t k = 0;
+        for (int64_t v = 0; v < nvert; ++v) {
+            int64_t d = off[v + 1] - off[v];
+            G->coin_at[v] = k;
+            k += d * d;
+        }
+    }
+    return OR_OK;
+}
+
+/* entry (r, c) of C_v */
+static cplx graph_coin(const graph *G, int64_t v, int64_t r, int64_t c)
+{
+    int64_t d = G->off[v + 1] - G->off[v];
+    if (G->coin_mode == 0) return (r == c ? -1.0 : 0.0) + 2.0 / (double)d;
+    return G->coins[G->coin_at[v] + r * d + c];
+}
+
+/* U = S (I (x) C): phi = C_v psi on each vertex, then phi(a) moves to partner[a] */
+static void graph_step_forward(const graph *G, const cplx *in, cplx *out)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < G->nvert; ++v) {
+        const int64_t o = G->off[v], d = G->off[v + 1] - o;
+        for (int64_t r = 0; r < d; ++r) {
+            cplx phi = 0;
+            for (int64_t c = 0; c < d; ++c) phi += graph_coin(G, v, r, c) * in[o + c];
+            out[G->partner[o + r]] = phi;   /* partner is a bijection: no races */
+        }
+    }
+}
+
+/* U^dagger = (I (x) C^dagger) S^dagger, and S^dagger = S (an involution) */
+static void graph_step_adjoint(const graph *G, const cplx *in, cplx *out)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < G->nvert; ++v) {
+        const int64_t o = G->off[v], d = G->off[v + 1] - o;
+        for (int64_t r = 0; r < d; ++r) {
+            cplx acc = 0;
+            for (int64_t c = 0; c < d; ++c) acc += conj(graph_coin(G, v, c, r)) * in[G->partner[o + c]];
+            out[o + r] = acc;
+        }
+    }
+}
+
+/* psi_out = U^T psi_in (or (U^dagger)^T); psi: narcs complex doubles in arc
+ * order.  psi_in and psi_out may alias. */
+int oracle_graph_evolve(int64_t nvert, const int64_t *off, const int64_t *partner, int coin_mode,
+                        const double *coins, const double *psi_in, int64_t T, int adjoint, double *psi_out)
+{
+    graph G = {0};
+    int st = graph_init(&G, nvert, off, partner, coin_mode, coins);
+    if (st) { free(G.coin_at); return st; }
+    if (T < 0 || (G.narcs && (!psi_in || !psi_out))) { free(G.coin_at); return OR_EINVAL; }
+    size_t n = (size_t)G.narcs;
+    cplx *a = malloc(sizeof(cplx) * (n ? n : 1)), *b = malloc(sizeof(cplx) * (n ? n : 1));
+    if (!a || !b) { free(a); free(b); free(G.coin_at); return OR_ENOMEM; }
+    if (n) memcpy(a, psi_in, sizeof(cplx) * n);
+    for (int64_t t = 0; t < T; ++t) {
+        if (adjoint) graph_step_adjoint(&G, a, b); else graph_step_forward(&G, a, b);
+        cplx *tmp = a; a = b; b = tmp;
+    }
+    if (n) memcpy(psi_out, a, sizeof(cplx) * n);
+    free(a); free(b); free(G.coin_at);
+    return OR_OK;
+}
+
+/* P(v) = sum over the arcs of v of |psi(a)|^2, norm = sum_v P(v) (Neumaier
+ * compensated, vertex order). */
+int oracle_graph_probabilities(int64_t nvert, const int64_t *off, const double *psi, double *P, double *norm)
+{
+    if (nvert < 1 || !off || !psi || !P) return OR_EINVAL;
+    const cplx *s = (const cplx *)psi;
+    double sum = 0.0, comp = 0.0;
+    for (int64_t v = 0; v < nvert; ++v) {
+        double p = 0.0;
+        for (int64_t a = off[v]; a < off[v + 1]; ++a) p += creal(s[a]) * creal(s[a]) + cimag(s[a]) * cimag(s[a]);
+        P[v] = p;
+        double t = sum + p;
+        comp += fabs(sum) >= fabs(p) ? (sum - t) + p : (p - t) + sum;
+        sum = t;
+    }
+    if (norm) *norm = sum + comp;
+    return OR_OK;
 }

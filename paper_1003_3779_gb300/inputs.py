@@ -17,6 +17,13 @@ the scenarios the library is built for):
 * ``torus_2d``         8192^2 torus, Grover or H(x)H, moving or flip-flop, T=1024
 * ``batch_1d``         4096 walks, N~U[256,65536], T~U[64,4096], theta~U[0,pi/2]
 * ``region_grad_2d``   1024^2 torus, Grover.diag(e^{i phi}), phi~U[-0.1,0.1], T=512
+* graphs (Sec. 2.1)    a random 4-regular graph (configuration model, 2^26
+                       vertices), the 8192^2 torus as a graph, and a power-law
+                       (Chung-Lu) graph with skewed degrees; Grover coin
+
+A graph walk's state is one amplitude per arc (vertex, edge end) in the arc
+form: the arcs of vertex v are off[v] .. off[v+1]-1 and partner[a] is the arc at
+the other end of a's edge.
 """
 from __future__ import annotations
 
@@ -136,3 +143,58 @@ def region_grad_phases(L: int = 1024, seed: int = 4, amp: float = 0.1) -> np.nda
 def region_rect(L: int = 1024, centre=(256, 256), size: int = 64):
     """(x0, y0, w, h) of the size x size square centred at ``centre``."""
     return (centre[0] - size // 2, centre[1] - size // 2, size, size)
+
+
+# ---------------------------------------------------------------- graphs
+def random_regular_arcs(nvert: int, degree: int, seed: int):
+    """Arc form (off, partner) of a random degree-regular multigraph by the
+    configuration model: vertex v owns arcs v*degree .. v*degree+degree-1 (its
+    edge ends), and a uniformly random perfect matching pairs all arcs into
+    edges (loops and parallel edges are kept).  nvert*degree must be even."""
+    A = int(nvert) * int(degree)
+    if A % 2:
+        raise ValueError("nvert * degree must be even")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    perm = rng.permutation(A).astype(np.int64)
+    partner = np.empty(A, dtype=np.int64)
+    partner[perm[0::2]] = perm[1::2]
+    partner[perm[1::2]] = perm[0::2]
+    off = np.arange(0, A + 1, degree, dtype=np.int64)
+    return off, partner
+
+
+def lattice_graph_arcs(Lx: int, Ly: int | None = None):
+    """The cycle Z_Lx (Ly None) or the torus Z_Lx x Z_Ly as a graph in arc form,
+    with the lattice's coin slots as arc slots: on the cycle vertex x has slot 0
+    (edge to x-1) and slot 1 (edge to x+1); on the torus vertex y*Lx + x has
+    slots +x, -x, +y, -y.  The graph walk on it is the flip-flop lattice walk."""
+    if Ly is None:
+        x = np.arange(Lx, dtype=np.int64)
+        partner = np.empty(2 * Lx, dtype=np.int64)
+        partner[2 * x] = 2 * ((x - 1) % Lx) + 1
+        partner[2 * x + 1] = 2 * ((x + 1) % Lx)
+        return np.arange(0, 2 * Lx + 1, 2, dtype=np.int64), partner
+    y, x = np.divmod(np.arange(Lx * Ly, dtype=np.int64), Lx)
+    right, left = y * Lx + (x + 1) % Lx, y * Lx + (x - 1) % Lx
+    up, down = ((y + 1) % Ly) * Lx + x, ((y - 1) % Ly) * Lx + x
+    v = y * Lx + x
+    partner = np.empty(4 * Lx * Ly, dtype=np.int64)
+    partner[4 * v] = 4 * right + 1
+    partner[4 * v + 1] = 4 * left
+    partner[4 * v + 2] = 4 * up + 3
+    partner[4 * v + 3] = 4 * down + 2
+    return np.arange(0, 4 * Lx * Ly + 1, 4, dtype=np.int64), partner
+
+
+def chung_lu_edges(nvert: int, mean_degree: float, exponent: float, seed: int) -> np.ndarray:
+    """Edge list (nedges, 2) of a Chung-Lu graph with power-law expected
+    degrees: vertex v has weight (v + 1)^(-1/(exponent - 1)); nvert*mean_degree/2
+    edges, each joining two vertices drawn in proportion to their weights
+    (loops, parallel edges and isolated vertices are kept)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    w = (np.arange(nvert, dtype=np.float64) + 1.0) ** (-1.0 / (exponent - 1.0))
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    m = int(round(nvert * mean_degree / 2))
+    ends = np.searchsorted(cdf, rng.uniform(0.0, 1.0, size=2 * m), side="right")
+    return np.minimum(ends, nvert - 1).astype(np.int64).reshape(m, 2)
