@@ -240,6 +240,80 @@ qw_status qw_probabilities_noalloc(const void *amp, qw_cdtype dtype, int coin_di
                                    void *P_out, qw_rdtype pdtype, double *norm_out,
                                    void *cuda_stream);
 
+/* ---------------------------------------------------------------- graphs */
+
+/* The walk on a general graph G = (V, E) (Sec. 2.1).  The local space of
+ * vertex v has one basis state |v, e> per edge e at v; the state holds one
+ * complex amplitude per such (vertex, edge end) pair, an "arc".  Arc form of
+ * a graph: the arcs of vertex v are off[v] .. off[v+1]-1 (its coin slots, in
+ * a fixed order), and partner[a] is the arc |v', e> at the other end of a's
+ * edge e = {v, v'}; a loop gives v two arcs that are each other's partner.
+ * One step is U = S (I (x) C):
+ *   phi(a) = sum_j C_v[i][j] psi(off[v] + j)   for a = off[v] + i,
+ *   psi'(partner[a]) = phi(a)                  (S|v,e> = |v',e>).
+ * On the cycle or torus with the lattice's coin slots as arc slots this is
+ * the flip-flop lattice walk. */
+typedef struct qw_gwalk qw_gwalk;   /* opaque, library-owned */
+
+/* Coins of a graph walk: QW_GCOIN_GROVER, C_v = (2/d(v)) J - I at every vertex
+ * (J all ones; no matrix is passed); QW_GCOIN_UNIFORM, one d x d matrix for a
+ * graph whose vertices all have degree d; QW_GCOIN_PER_VERTEX, one d(v) x d(v)
+ * matrix per vertex, concatenated in vertex order. */
+typedef enum { QW_GCOIN_GROVER = 0, QW_GCOIN_UNIFORM = 1, QW_GCOIN_PER_VERTEX = 2 } qw_gcoin;
+
+/* Arc form from an edge list (host memory): edges holds nedges pairs (u, w) of
+ * vertex indices in [0, nvert).  Each vertex's slots follow the order in which
+ * its edge ends appear in the list (end u of pair k before end w).  off:
+ * nvert + 1 entries, partner: 2*nedges entries, written by the call.
+ * QW_EINVAL for a vertex index out of range. */
+qw_status qw_graph_arcs(int64_t nvert, int64_t nedges, const int64_t *edges, int64_t *off, int64_t *partner);
+
+/* Create a graph walk (nvert >= 1 vertices, arcs off[nvert] < 2^31) from the
+ * arc form in host memory (copied; the caller keeps its arrays).  The state
+ * starts at zero and the coin is Grover.  prec: QW_F64 or QW_F32 (others
+ * QW_EUNSUPPORTED).  QW_EINVAL when off is not non-decreasing from 0 or
+ * partner is not an involution of [0, off[nvert]).  Device memory: two state
+ * buffers (A amplitudes each), off, partner and, for graphs that are not
+ * regular of degree 2 or 4, the vertex of each arc (4 bytes per arc). */
+qw_status qw_gwalk_create(int64_t nvert, const int64_t *off, const int64_t *partner, qw_precision prec,
+                          void *cuda_stream, qw_gwalk **out);
+qw_status qw_gwalk_destroy(qw_gwalk *g);
+
+/* Set the coin (see qw_gcoin).  coins: row-major complex doubles (re/im),
+ * d*d entries (uniform) or sum_v d(v)^2 entries (per vertex), host or device
+ * (on_device); NULL for Grover.  QW_EINVAL for a uniform coin on a graph that
+ * is not regular. */
+qw_status qw_gwalk_set_coin(qw_gwalk *g, qw_gcoin mode, const double *coins, int on_device);
+
+/* Replace / read the state: off[nvert] complex amplitudes in arc order, of
+ * type dtype, host or device (on_device). */
+qw_status qw_gwalk_set_state(qw_gwalk *g, const void *amp, qw_cdtype dtype, int on_device);
+qw_status qw_gwalk_get_state(qw_gwalk *g, void *amp_out, qw_cdtype dtype, int on_device);
+
+/* Apply U^T, or (U^dagger)^T = ((I (x) C^dagger) S)^T.  One kernel per step
+ * (plus, for the Grover coin, a pre-pass over the vertices of degree > 32). */
+qw_status qw_gwalk_step(qw_gwalk *g, int64_t T);
+qw_status qw_gwalk_step_adjoint(qw_gwalk *g, int64_t T);
+
+/* P(v) = sum over the arcs of v of |psi(a)|^2 (nvert values of type pdtype,
+ * host or device; may be NULL) and the norm sum_v P(v), accumulated in double
+ * in a fixed order, into *norm_out (host; may be NULL). */
+qw_status qw_gwalk_probabilities(qw_gwalk *g, void *P_out, qw_rdtype pdtype, int on_device, double *norm_out);
+
+/* Form of the forward step: 0 push (each arc's thread reads its own vertex and
+ * writes the partner arc), 1 pull (reads the partner's vertex, writes its own
+ * arc); -1 restores the default (push).  Both give the same bits. */
+qw_status qw_gwalk_set_variant(qw_gwalk *g, int variant);
+qw_status qw_gwalk_get_variant(const qw_gwalk *g, int *variant);
+
+/* Time both forms on the current state (which is saved and restored), keep
+ * the faster, and write a JSON report. */
+qw_status qw_gwalk_autotune(qw_gwalk *g, char *report, size_t report_len);
+
+qw_status qw_gwalk_synchronize(qw_gwalk *g);
+int64_t qw_gwalk_narcs(const qw_gwalk *g);   /* -1 for NULL */
+const char *qw_gwalk_last_error(const qw_gwalk *g);
+
 /* ---------------------------------------------------------------- batches */
 
 /* A batch of independent 1D walks on cycles (Sec. 2.2), walk i with N[i]

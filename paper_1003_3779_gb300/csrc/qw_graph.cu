@@ -1,0 +1,664 @@
+// qw_graph.cu -- the coined walk on a general graph (Sec. 2.1).
+//
+// The local space of vertex v has one basis state |v, e> per edge e at v, so
+// the state is one amplitude per (vertex, edge end): an arc.  Arc form: the
+// arcs of v are off[v] .. off[v+1]-1 (its coin slots), and partner[a] is the
+// arc at the other end of a's edge.  One step is U = S (I (x) C):
+//
+//   phi(a) = sum_j C_v[i][j] psi(off[v] + j)      (a = off[v] + i, coin at v)
+//   psi'(partner[a]) = phi(a)                     (S|v,e> = |v',e>)
+//
+// and the adjoint U^dagger = (I (x) C^dagger) S, since S is an involution:
+//
+//   psi'(a) = sum_j conj(C_v[j][i]) psi(partner[off[v] + j]).
+//
+// There is no locality to block over in a general graph, so each step is one
+// pass over the arcs, bound by HBM: one thread per arc, which reads its
+// vertex's amplitudes (neighbouring threads share them through L1) and writes
+// one amplitude.  Two forms of the forward step:
+//   push (variant 0): thread a reads its own vertex (coalesced) and writes
+//     psi'(partner[a]) (a scattered 8 or 16 B store);
+//   pull (variant 1): thread a reads the vertex of partner[a] (a scattered
+//     read of that vertex's arcs) and writes psi'(a) (coalesced).
+// On a graph whose arcs are ordered with locality (lattices) both stream; on a
+// random graph the scattered side costs whole 32-byte sectors, and which side
+// is cheaper is measured (qw_gwalk_autotune).
+//
+// Regular graphs of degree 2 or 4 find an arc's vertex by division; others
+// read it from a per-arc vertex index.  The Grover coin (2/d) J - I needs the
+// vertex sum of the amplitudes; vertices of degree above GR_HEAVY get it from
+// a one-block-per-vertex pre-pass instead of every arc summing d values.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "qw_handle.h"
+
+namespace qw {
+
+static constexpr int GR_THREADS = 256;
+static constexpr int GR_HEAVY = 32;
+static constexpr int GR_RED_BLOCKS = 152 * 4;
+
+template <class R>
+struct GraphArgs {
+    int A;                     // number of arcs
+    const int *src;            // vertex of each arc (irregular graphs)
+    const int *off;            // first arc of each vertex, nvert + 1 entries
+    const int *partner;        // the shift: arc at the other end of the edge
+    const Cx<R> *coins;        // uniform: one d x d; per vertex: concatenated blocks
+    const long long *coff;     // per vertex: first entry of the vertex's block
+    const Cx<R> *vsum;         // Grover: amplitude sums of the heavy vertices
+};
+
+template <int DR, class R>
+__device__ __forceinline__ void vertex_of(const GraphArgs<R> &g, int a, int &v, int &o, int &d) {
+    if constexpr (DR > 0) {
+        v = a / DR;
+        o = v * DR;
+        d = DR;
+    } else {
+        v = __ldg(g.src + a);
+        o = __ldg(g.off + v);
+        d = __ldg(g.off + v + 1) - o;
+    }
+}
+
+// Row i of the coin at v applied to the vertex's amplitudes x_j: x_j =
+// psi(o + j) for the forward step, psi(partner[o + j]) for the adjoint, whose
+// coin is C_v^dagger (row i of C^dagger = conjugated column i of C).
+template <int MODE, int DR, int ADJ, class R>
+__device__ __forceinline__ Cx<R> coin_row(const GraphArgs<R> &g, const Cx<R> *__restrict__ in, int v, int o, int d,
+                                          int i) {
+    auto x = [&](int k) -> Cx<R> { return ADJ ? in[__ldg(g.partner + k)] : in[k]; };
+    if constexpr (MODE == QW_GCOIN_GROVER) {
+        Cx<R> s{R(0), R(0)};
+        if (DR == 0 && d > GR_HEAVY) {
+            s = g.vsum[v];
+        } else {
+            for (int j = 0; j < d; ++j) s = cadd(s, x(o + j));
+        }
+        return csub(rmul(R(2) / R(d), s), x(o + i));
+    } else {
+        const Cx<R> *C = MODE == QW_GCOIN_UNIFORM ? g.coins : g.coins + g.coff[v];
+        Cx<R> acc{R(0), R(0)};
+        for (int j = 0; j < d; ++j) {
+            if (ADJ) acc = cadd(acc, conjmul(C[j * d + i], x(o + j)));
+            else acc = cfma(C[i * d + j], x(o + j), acc);
+        }
+        return acc;
+    }
+}
+
+// forward, push: psi'(partner[a]) = row i of C_v applied to psi at v
+template <class R, int MODE, int DR>
+__global__ void __launch_bounds__(GR_THREADS)
+k_graph_push(GraphArgs<R> g, const Cx<R> *__restrict__ in, Cx<R> *__restrict__ out) {
+    const int a = blockIdx.x * GR_THREADS + threadIdx.x;
+    if (a >= g.A) return;
+    int v, o, d;
+    vertex_of<DR>(g, a, v, o, d);
+    out[__ldg(g.partner + a)] = coin_row<MODE, DR, 0>(g, in, v, o, d, a - o);
+}
+
+// forward, pull: psi'(a) = phi(partner[a]), computed at the partner's vertex
+template <class R, int MODE, int DR>
+__global__ void __launch_bounds__(GR_THREADS)
+k_graph_pull(GraphArgs<R> g, const Cx<R> *__restrict__ in, Cx<R> *__restrict__ out) {
+    const int a = blockIdx.x * GR_THREADS + threadIdx.x;
+    if (a >= g.A) return;
+    const int b = __ldg(g.partner + a);
+    int v, o, d;
+    vertex_of<DR>(g, b, v, o, d);
+    out[a] = coin_row<MODE, DR, 0>(g, in, v, o, d, b - o);
+}
+
+// adjoint: psi'(a) = row i of C_v^dagger applied to (S psi) at v
+template <class R, int MODE, int DR>
+__global__ void __launch_bounds__(GR_THREADS)
+k_graph_adjoint(GraphArgs<R> g, const Cx<R> *__restrict__ in, Cx<R> *__restrict__ out) {
+    const int a = blockIdx.x * GR_THREADS + threadIdx.x;
+    if (a >= g.A) return;
+    int v, o, d;
+    vertex_of<DR>(g, a, v, o, d);
+    out[a] = coin_row<MODE, DR, 1>(g, in, v, o, d, a - o);
+}
+
+// Grover pre-pass: the amplitude sum of each heavy vertex (of psi, or of S psi
+// for the adjoint), one block per vertex, threads over fixed strided arcs, then
+// a fixed shuffle / shared-memory tree: the same bits on every run.
+template <class R, int ADJ>
+__global__ void __launch_bounds__(GR_THREADS)
+k_graph_heavy(GraphArgs<R> g, const int *__restrict__ heavy, int nheavy, const Cx<R> *__restrict__ in,
+              Cx<R> *__restrict__ vsum) {
+    __shared__ R sh[2][GR_THREADS / 32];
+    for (int h = blockIdx.x; h < nheavy; h += gridDim.x) {
+        const int v = heavy[h];
+        const int o = g.off[v], d = g.off[v + 1] - o;
+        Cx<R> s{R(0), R(0)};
+        for (int j = threadIdx.x; j < d; j += GR_THREADS) s = cadd(s, ADJ ? in[g.partner[o + j]] : in[o + j]);
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) {
+            s.re += __shfl_down_sync(0xffffffffu, s.re, m);
+            s.im += __shfl_down_sync(0xffffffffu, s.im, m);
+        }
+        if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = s.re; sh[1][threadIdx.x >> 5] = s.im; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            Cx<R> t{R(0), R(0)};
+            for (int w = 0; w < GR_THREADS / 32; ++w) { t.re += sh[0][w]; t.im += sh[1][w]; }
+            vsum[v] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// P(v) = sum over the arcs of v of |psi(a)|^2 (in the compute precision), and
+// the norm in double over a fixed grid: per-thread strided vertices, a block
+// tree, then one warp over the block partials in order.
+template <class R, class PO>
+__global__ void __launch_bounds__(GR_THREADS)
+k_graph_marginals(const int *__restrict__ off, int nvert, const Cx<R> *__restrict__ psi, PO *P, double *partials) {
+    __shared__ double sh[GR_THREADS / 32];
+    double acc = 0.0;
+    for (int v = blockIdx.x * GR_THREADS + threadIdx.x; v < nvert; v += gridDim.x * GR_THREADS) {
+        R p = R(0);
+        for (int a = off[v]; a < off[v + 1]; ++a) p += psi[a].re * psi[a].re + psi[a].im * psi[a].im;
+        if (P) P[v] = (PO)p;
+        acc += (double)p;
+    }
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, m);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < GR_THREADS / 32; ++w) t += sh[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_graph_norm(const double *partials, int n, double *out) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) v += partials[i];
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) v += __shfl_down_sync(0xffffffffu, v, m);
+    if (threadIdx.x == 0) *out = v;
+}
+
+// element conversion between caller and compute precision
+template <class RI, class RO>
+__global__ void k_graph_convert(const Cx<RI> *__restrict__ in, Cx<RO> *__restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)GR_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * GR_THREADS)
+        out[i] = Cx<RO>{(RO)in[i].re, (RO)in[i].im};
+}
+
+}  // namespace qw
+
+using namespace qw;
+
+struct qw_gwalk {
+    int64_t nvert = 0;
+    int A = 0;
+    int prec = QW_F32;
+    int dreg = 0;                 // common degree when every vertex has it, else 0
+    int maxdeg = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<int> deg;         // host copy of the degrees
+    int *off_dev = nullptr, *src_dev = nullptr, *partner_dev = nullptr;
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    int mode = QW_GCOIN_GROVER;
+    void *coins_dev = nullptr;
+    size_t coins_bytes = 0;
+    long long *coff_dev = nullptr;
+    int *heavy_dev = nullptr;
+    int nheavy = 0;
+    void *vsum_dev = nullptr;
+    double *partials = nullptr, *norm_dev = nullptr;
+    void *p_dev = nullptr;
+    size_t p_bytes = 0;
+    void *staging = nullptr;
+    size_t staging_bytes = 0;
+    int variant = -1;             // -1: default (push)
+    std::string err;
+};
+
+namespace {
+
+qw_status gfail(qw_gwalk *g, qw_status st, const std::string &m) {
+    if (g) g->err = m;
+    return st;
+}
+
+qw_status gcuda(qw_gwalk *g, cudaError_t e, const char *where) {
+    (void)cudaGetLastError();
+    return gfail(g, e == cudaErrorMemoryAllocation ? QW_ENOMEM : QW_ECUDA,
+                 std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+size_t amp_bytes(const qw_gwalk *g) { return g->prec == QW_F64 ? 16 : 8; }
+
+qw_status ensure_staging(qw_gwalk *g, size_t bytes) {
+    if (g->staging_bytes >= bytes) return QW_OK;
+    if (g->staging) { cudaStreamSynchronize(g->stream); cudaFree(g->staging); g->staging = nullptr; g->staging_bytes = 0; }
+    cudaError_t e = dev_alloc(&g->staging, bytes);
+    if (e != cudaSuccess) return gcuda(g, e, "graph staging allocation");
+    g->staging_bytes = bytes;
+    return QW_OK;
+}
+
+template <class R>
+GraphArgs<R> args_of(const qw_gwalk *g) {
+    GraphArgs<R> a{};
+    a.A = g->A;
+    a.src = g->src_dev;
+    a.off = g->off_dev;
+    a.partner = g->partner_dev;
+    a.coins = static_cast<const Cx<R> *>(g->coins_dev);
+    a.coff = g->coff_dev;
+    a.vsum = static_cast<const Cx<R> *>(g->vsum_dev);
+    return a;
+}
+
+// kernel: 0 push, 1 pull, 2 adjoint
+template <class R, int MODE, int DR>
+cudaError_t launch_mode_dr(const GraphArgs<R> &a, int kernel, const Cx<R> *in, Cx<R> *out, cudaStream_t s) {
+    const unsigned blocks = (unsigned)((a.A + GR_THREADS - 1) / GR_THREADS);
+    if (kernel == 0) k_graph_push<R, MODE, DR><<<blocks, GR_THREADS, 0, s>>>(a, in, out);
+    else if (kernel == 1) k_graph_pull<R, MODE, DR><<<blocks, GR_THREADS, 0, s>>>(a, in, out);
+    else k_graph_adjoint<R, MODE, DR><<<blocks, GR_THREADS, 0, s>>>(a, in, out);
+    return cudaGetLastError();
+}
+
+template <class R, int MODE>
+cudaError_t launch_mode(const qw_gwalk *g, const GraphArgs<R> &a, int kernel, const Cx<R> *in, Cx<R> *out) {
+    if (g->dreg == 2) return launch_mode_dr<R, MODE, 2>(a, kernel, in, out, g->stream);
+    if (g->dreg == 4) return launch_mode_dr<R, MODE, 4>(a, kernel, in, out, g->stream);
+    return launch_mode_dr<R, MODE, 0>(a, kernel, in, out, g->stream);
+}
+
+template <class R>
+cudaError_t graph_step(qw_gwalk *g, int kernel) {
+    if (g->A == 0) return cudaSuccess;
+    GraphArgs<R> a = args_of<R>(g);
+    const Cx<R> *in = static_cast<const Cx<R> *>(g->buf[g->cur]);
+    Cx<R> *out = static_cast<Cx<R> *>(g->buf[g->cur ^ 1]);
+    if (g->mode == QW_GCOIN_GROVER && g->nheavy && g->dreg != 2 && g->dreg != 4) {
+        const int blocks = std::min(g->nheavy, 152 * 8);
+        if (kernel == 2)
+            k_graph_heavy<R, 1><<<blocks, GR_THREADS, 0, g->stream>>>(a, g->heavy_dev, g->nheavy, in, (Cx<R> *)g->vsum_dev);
+        else
+            k_graph_heavy<R, 0><<<blocks, GR_THREADS, 0, g->stream>>>(a, g->heavy_dev, g->nheavy, in, (Cx<R> *)g->vsum_dev);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    switch (g->mode) {
+        case QW_GCOIN_GROVER: return launch_mode<R, QW_GCOIN_GROVER>(g, a, kernel, in, out);
+        case QW_GCOIN_UNIFORM: return launch_mode<R, QW_GCOIN_UNIFORM>(g, a, kernel, in, out);
+        default: return launch_mode<R, QW_GCOIN_PER_VERTEX>(g, a, kernel, in, out);
+    }
+}
+
+qw_status run_graph(qw_gwalk *g, int64_t T, int adj) {
+    if (T < 0) return gfail(g, QW_EINVAL, "T must be >= 0");
+    const int kernel = adj ? 2 : (g->variant == 1 ? 1 : 0);
+    for (int64_t t = 0; t < T; ++t) {
+        cudaError_t e = g->prec == QW_F64 ? graph_step<double>(g, kernel) : graph_step<float>(g, kernel);
+        if (e != cudaSuccess) return gcuda(g, e, "graph step launch");
+        g->cur ^= 1;
+    }
+    return QW_OK;
+}
+
+template <class RI, class RO>
+cudaError_t convert(const void *in, void *out, long long n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const long long want = (n + GR_THREADS - 1) / GR_THREADS;
+    const unsigned blocks = (unsigned)std::min<long long>(want, 152 * 16);
+    k_graph_convert<RI, RO><<<blocks, GR_THREADS, 0, s>>>(static_cast<const Cx<RI> *>(in), static_cast<Cx<RO> *>(out), n);
+    return cudaGetLastError();
+}
+
+// doubles (re/im) -> compute precision, device to device
+cudaError_t from_doubles(const qw_gwalk *g, const void *in, void *out, long long n) {
+    if (g->prec == QW_F64)
+        return cudaMemcpyAsync(out, in, (size_t)n * 16, cudaMemcpyDeviceToDevice, g->stream);
+    return convert<double, float>(in, out, n, g->stream);
+}
+
+void free_all(qw_gwalk *g) {
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    for (void *p : {(void *)g->off_dev, (void *)g->src_dev, (void *)g->partner_dev, g->buf[0], g->buf[1], g->coins_dev,
+                    (void *)g->coff_dev, (void *)g->heavy_dev, g->vsum_dev, (void *)g->partials, (void *)g->norm_dev,
+                    g->p_dev, g->staging})
+        if (p) cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+qw_status qw_graph_arcs(int64_t nvert, int64_t nedges, const int64_t *edges, int64_t *off, int64_t *partner) {
+    if (nvert < 1 || nedges < 0 || !off || (nedges && (!edges || !partner))) return QW_EINVAL;
+    for (int64_t k = 0; k < 2 * nedges; ++k)
+        if (edges[k] < 0 || edges[k] >= nvert) return QW_EINVAL;
+    // count the edge ends at each vertex, prefix-sum into first arcs, then hand
+    // out slots in list order and pair the two ends of every edge
+    std::vector<int64_t> next((size_t)nvert + 1, 0);
+    for (int64_t k = 0; k < 2 * nedges; ++k) ++next[(size_t)edges[k] + 1];
+    for (int64_t v = 0; v < nvert; ++v) next[(size_t)v + 1] += next[(size_t)v];
+    std::memcpy(off, next.data(), sizeof(int64_t) * ((size_t)nvert + 1));
+    for (int64_t e = 0; e < nedges; ++e) {
+        const int64_t a = next[(size_t)edges[2 * e]]++;
+        const int64_t b = next[(size_t)edges[2 * e + 1]]++;
+        partner[a] = b;
+        partner[b] = a;
+    }
+    return QW_OK;
+}
+
+qw_status qw_gwalk_create(int64_t nvert, const int64_t *off, const int64_t *partner, qw_precision prec,
+                          void *cuda_stream, qw_gwalk **out) {
+    if (!out) return QW_EINVAL;
+    *out = nullptr;
+    if (nvert < 1 || !off) return QW_EINVAL;
+    if (prec != QW_F32 && prec != QW_F64) return QW_EUNSUPPORTED;
+    if (nvert >= (int64_t(1) << 31) || off[nvert] >= (int64_t(1) << 31)) return QW_EUNSUPPORTED;
+    if (off[0] != 0) return QW_EINVAL;
+    for (int64_t v = 0; v < nvert; ++v)
+        if (off[v + 1] < off[v]) return QW_EINVAL;
+    const int64_t A = off[nvert];
+    if (A && !partner) return QW_EINVAL;
+    for (int64_t a = 0; a < A; ++a)
+        if (partner[a] < 0 || partner[a] >= A || partner[partner[a]] != a) return QW_EINVAL;
+
+    qw_gwalk *g = new (std::nothrow) qw_gwalk();
+    if (!g) return QW_ENOMEM;
+    g->nvert = nvert;
+    g->A = (int)A;
+    g->prec = prec;
+    g->stream = static_cast<cudaStream_t>(cuda_stream);
+    g->deg.resize((size_t)nvert);
+    std::vector<int> offi((size_t)nvert + 1), heavy;
+    for (int64_t v = 0; v <= nvert; ++v) offi[(size_t)v] = (int)off[v];
+    for (int64_t v = 0; v < nvert; ++v) {
+        const int d = (int)(off[v + 1] - off[v]);
+        g->deg[(size_t)v] = d;
+        g->maxdeg = std::max(g->maxdeg, d);
+        if (d > GR_HEAVY) heavy.push_back((int)v);
+    }
+    g->dreg = g->deg[0];
+    for (int64_t v = 1; v < nvert; ++v)
+        if (g->deg[(size_t)v] != g->dreg) { g->dreg = 0; break; }
+    const bool need_src = g->dreg != 2 && g->dreg != 4;
+    std::vector<int> pi((size_t)A), src(need_src ? (size_t)A : 0);
+    for (int64_t a = 0; a < A; ++a) pi[(size_t)a] = (int)partner[a];
+    if (need_src)
+        for (int64_t v = 0; v < nvert; ++v)
+            for (int64_t a = off[v]; a < off[v + 1]; ++a) src[(size_t)a] = (int)v;
+    g->nheavy = (int)heavy.size();
+
+    const size_t sb = (size_t)std::max<int64_t>(A, 1) * amp_bytes(g);
+    cudaError_t e = dev_alloc((void **)&g->off_dev, sizeof(int) * offi.size());
+    if (e == cudaSuccess) e = dev_alloc((void **)&g->partner_dev, sizeof(int) * std::max<size_t>(pi.size(), 1));
+    if (e == cudaSuccess && need_src) e = dev_alloc((void **)&g->src_dev, sizeof(int) * std::max<size_t>(src.size(), 1));
+    if (e == cudaSuccess) e = dev_alloc(&g->buf[0], sb);
+    if (e == cudaSuccess) e = dev_alloc(&g->buf[1], sb);
+    if (e == cudaSuccess) e = dev_alloc((void **)&g->partials, sizeof(double) * GR_RED_BLOCKS);
+    if (e == cudaSuccess) e = dev_alloc((void **)&g->norm_dev, sizeof(double));
+    if (e == cudaSuccess && g->nheavy) e = dev_alloc((void **)&g->heavy_dev, sizeof(int) * heavy.size());
+    if (e == cudaSuccess && g->nheavy) e = dev_alloc(&g->vsum_dev, (size_t)nvert * amp_bytes(g));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->off_dev, offi.data(), sizeof(int) * offi.size(), cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess && A)
+        e = cudaMemcpyAsync(g->partner_dev, pi.data(), sizeof(int) * pi.size(), cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess && need_src && A)
+        e = cudaMemcpyAsync(g->src_dev, src.data(), sizeof(int) * src.size(), cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess && g->nheavy)
+        e = cudaMemcpyAsync(g->heavy_dev, heavy.data(), sizeof(int) * heavy.size(), cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->buf[0], 0, sb, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);   // the host vectors go out of scope
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        const qw_status st = e == cudaErrorMemoryAllocation ? QW_ENOMEM : QW_ECUDA;
+        free_all(g);
+        delete g;
+        return st;
+    }
+    *out = g;
+    return QW_OK;
+}
+
+qw_status qw_gwalk_destroy(qw_gwalk *g) {
+    if (!g) return QW_OK;
+    free_all(g);
+    delete g;
+    return QW_OK;
+}
+
+const char *qw_gwalk_last_error(const qw_gwalk *g) { return g ? g->err.c_str() : "null handle"; }
+
+int64_t qw_gwalk_narcs(const qw_gwalk *g) { return g ? g->A : -1; }
+
+qw_status qw_gwalk_set_coin(qw_gwalk *g, qw_gcoin mode, const double *coins, int on_device) {
+    if (!g) return QW_EINVAL;
+    if (mode == QW_GCOIN_GROVER) { g->mode = mode; return QW_OK; }
+    if (mode != QW_GCOIN_UNIFORM && mode != QW_GCOIN_PER_VERTEX) return gfail(g, QW_EINVAL, "unknown coin mode");
+    if (!coins) return gfail(g, QW_EINVAL, "coins is NULL");
+    long long n = 0;
+    std::vector<long long> coff;
+    if (mode == QW_GCOIN_UNIFORM) {
+        if (g->dreg == 0) return gfail(g, QW_EINVAL, "a uniform coin needs a regular graph");
+        n = (long long)g->dreg * g->dreg;
+    } else {
+        coff.resize((size_t)g->nvert);
+        for (int64_t v = 0; v < g->nvert; ++v) {
+            coff[(size_t)v] = n;
+            n += (long long)g->deg[(size_t)v] * g->deg[(size_t)v];
+        }
+    }
+    const size_t want = (size_t)std::max<long long>(n, 1) * amp_bytes(g);
+    cudaError_t e = cudaSuccess;
+    if (g->coins_bytes < want) {
+        cudaStreamSynchronize(g->stream);
+        cudaFree(g->coins_dev);
+        g->coins_dev = nullptr;
+        g->coins_bytes = 0;
+        if ((e = dev_alloc(&g->coins_dev, want)) != cudaSuccess) return gcuda(g, e, "graph coin allocation");
+        g->coins_bytes = want;
+    }
+    if (mode == QW_GCOIN_PER_VERTEX && !g->coff_dev) {
+        if ((e = dev_alloc((void **)&g->coff_dev, sizeof(long long) * coff.size())) != cudaSuccess)
+            return gcuda(g, e, "graph coin offsets");
+        e = cudaMemcpyAsync(g->coff_dev, coff.data(), sizeof(long long) * coff.size(), cudaMemcpyHostToDevice, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) return gcuda(g, e, "graph coin offsets");
+    }
+    if (n) {
+        const void *src = coins;
+        if (!on_device) {
+            qw_status st = ensure_staging(g, (size_t)n * 16);
+            if (st != QW_OK) return st;
+            if ((e = cudaMemcpyAsync(g->staging, coins, (size_t)n * 16, cudaMemcpyHostToDevice, g->stream)) != cudaSuccess)
+                return gcuda(g, e, "graph coin copy");
+            src = g->staging;
+        }
+        if ((e = from_doubles(g, src, g->coins_dev, n)) != cudaSuccess) return gcuda(g, e, "graph coin conversion");
+        if (!on_device && (e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return gcuda(g, e, "graph coin copy");
+    }
+    g->mode = mode;
+    return QW_OK;
+}
+
+qw_status qw_gwalk_set_state(qw_gwalk *g, const void *amp, qw_cdtype dtype, int on_device) {
+    if (!g) return QW_EINVAL;
+    if (!amp || (dtype != QW_C128 && dtype != QW_C64)) return gfail(g, QW_EINVAL, "bad state buffer or dtype");
+    const long long n = g->A;
+    const size_t eb = dtype == QW_C128 ? 16 : 8;
+    const bool same = (g->prec == QW_F64) == (dtype == QW_C128);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaSuccess;
+    if (n == 0) return QW_OK;
+    if (same) {
+        e = cudaMemcpyAsync(g->buf[g->cur], amp, (size_t)n * eb, kind, g->stream);
+    } else {
+        const void *src = amp;
+        if (!on_device) {
+            qw_status st = ensure_staging(g, (size_t)n * eb);
+            if (st != QW_OK) return st;
+            e = cudaMemcpyAsync(g->staging, amp, (size_t)n * eb, kind, g->stream);
+            src = g->staging;
+        }
+        if (e == cudaSuccess)
+            e = dtype == QW_C128 ? convert<double, float>(src, g->buf[g->cur], n, g->stream)
+                                 : convert<float, double>(src, g->buf[g->cur], n, g->stream);
+    }
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return gcuda(g, e, "graph state upload");
+    return QW_OK;
+}
+
+qw_status qw_gwalk_get_state(qw_gwalk *g, void *amp_out, qw_cdtype dtype, int on_device) {
+    if (!g) return QW_EINVAL;
+    if (!amp_out || (dtype != QW_C128 && dtype != QW_C64)) return gfail(g, QW_EINVAL, "bad state buffer or dtype");
+    const long long n = g->A;
+    const size_t eb = dtype == QW_C128 ? 16 : 8;
+    const bool same = (g->prec == QW_F64) == (dtype == QW_C128);
+    cudaError_t e = cudaSuccess;
+    if (n == 0) return QW_OK;
+    if (same) {
+        e = cudaMemcpyAsync(amp_out, g->buf[g->cur], (size_t)n * eb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            g->stream);
+    } else {
+        void *dst = amp_out;
+        if (!on_device) {
+            qw_status st = ensure_staging(g, (size_t)n * eb);
+            if (st != QW_OK) return st;
+            dst = g->staging;
+        }
+        e = dtype == QW_C128 ? convert<float, double>(g->buf[g->cur], dst, n, g->stream)
+                             : convert<double, float>(g->buf[g->cur], dst, n, g->stream);
+        if (e == cudaSuccess && !on_device)
+            e = cudaMemcpyAsync(amp_out, g->staging, (size_t)n * eb, cudaMemcpyDeviceToHost, g->stream);
+    }
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return gcuda(g, e, "graph state download");
+    return QW_OK;
+}
+
+qw_status qw_gwalk_step(qw_gwalk *g, int64_t T) {
+    if (!g) return QW_EINVAL;
+    return run_graph(g, T, 0);
+}
+
+qw_status qw_gwalk_step_adjoint(qw_gwalk *g, int64_t T) {
+    if (!g) return QW_EINVAL;
+    return run_graph(g, T, 1);
+}
+
+qw_status qw_gwalk_probabilities(qw_gwalk *g, void *P_out, qw_rdtype pdtype, int on_device, double *norm_out) {
+    if (!g) return QW_EINVAL;
+    if (pdtype != QW_R64 && pdtype != QW_R32) return gfail(g, QW_EINVAL, "bad probability dtype");
+    const size_t pb = (size_t)g->nvert * (pdtype == QW_R32 ? 4 : 8);
+    void *pdst = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (P_out) {
+        if (on_device) {
+            pdst = P_out;
+        } else {
+            if (g->p_bytes < pb) {
+                cudaStreamSynchronize(g->stream);
+                cudaFree(g->p_dev);
+                g->p_dev = nullptr;
+                g->p_bytes = 0;
+                if ((e = dev_alloc(&g->p_dev, pb)) != cudaSuccess) return gcuda(g, e, "graph probability buffer");
+                g->p_bytes = pb;
+            }
+            pdst = g->p_dev;
+        }
+    }
+    const int nv = (int)g->nvert;
+    const bool f64 = g->prec == QW_F64;
+    if (pdtype == QW_R32) {
+        if (f64) k_graph_marginals<double, float><<<GR_RED_BLOCKS, GR_THREADS, 0, g->stream>>>(
+                     g->off_dev, nv, (const Cx<double> *)g->buf[g->cur], (float *)pdst, g->partials);
+        else k_graph_marginals<float, float><<<GR_RED_BLOCKS, GR_THREADS, 0, g->stream>>>(
+                 g->off_dev, nv, (const Cx<float> *)g->buf[g->cur], (float *)pdst, g->partials);
+    } else {
+        if (f64) k_graph_marginals<double, double><<<GR_RED_BLOCKS, GR_THREADS, 0, g->stream>>>(
+                     g->off_dev, nv, (const Cx<double> *)g->buf[g->cur], (double *)pdst, g->partials);
+        else k_graph_marginals<float, double><<<GR_RED_BLOCKS, GR_THREADS, 0, g->stream>>>(
+                 g->off_dev, nv, (const Cx<float> *)g->buf[g->cur], (double *)pdst, g->partials);
+    }
+    k_graph_norm<<<1, 32, 0, g->stream>>>(g->partials, GR_RED_BLOCKS, g->norm_dev);
+    if ((e = cudaGetLastError()) != cudaSuccess) return gcuda(g, e, "graph marginals launch");
+    if (P_out && !on_device)
+        if ((e = cudaMemcpyAsync(P_out, pdst, pb, cudaMemcpyDeviceToHost, g->stream)) != cudaSuccess)
+            return gcuda(g, e, "graph probability download");
+    if (norm_out) {
+        if ((e = cudaMemcpyAsync(norm_out, g->norm_dev, sizeof(double), cudaMemcpyDeviceToHost, g->stream)) != cudaSuccess)
+            return gcuda(g, e, "graph norm download");
+    }
+    if ((norm_out || (P_out && !on_device)) && (e = cudaStreamSynchronize(g->stream)) != cudaSuccess)
+        return gcuda(g, e, "graph probabilities");
+    return QW_OK;
+}
+
+qw_status qw_gwalk_set_variant(qw_gwalk *g, int variant) {
+    if (!g) return QW_EINVAL;
+    if (variant < -1 || variant > 1) return gfail(g, QW_EINVAL, "variant must be -1 (default), 0 (push) or 1 (pull)");
+    g->variant = variant;
+    return QW_OK;
+}
+
+qw_status qw_gwalk_get_variant(const qw_gwalk *g, int *variant) {
+    if (!g || !variant) return QW_EINVAL;
+    *variant = g->variant == 1 ? 1 : 0;
+    return QW_OK;
+}
+
+qw_status qw_gwalk_autotune(qw_gwalk *g, char *report, size_t report_len) {
+    if (!g) return QW_EINVAL;
+    // time a few steps of each forward form on the current state and keep the
+    // faster; the state is saved first and put back afterwards
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const size_t sb = (size_t)g->A * amp_bytes(g);
+    qw_status st = ensure_staging(g, std::max<size_t>(sb, 16));
+    if (st != QW_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(g->staging, g->buf[g->cur], sb, cudaMemcpyDeviceToDevice, g->stream);
+    float ms[2] = {0.f, 0.f};
+    const int saved = g->variant;
+    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+        g->variant = v;
+        if (run_graph(g, 2, 0) != QW_OK) { e = cudaErrorLaunchFailure; break; }
+        cudaEventRecord(e0, g->stream);
+        if (run_graph(g, 6, 0) != QW_OK) { e = cudaErrorLaunchFailure; break; }
+        cudaEventRecord(e1, g->stream);
+        if ((e = cudaEventSynchronize(e1)) == cudaSuccess) cudaEventElapsedTime(&ms[v], e0, e1);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->buf[g->cur], g->staging, sb, cudaMemcpyDeviceToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) { g->variant = saved; return gcuda(g, e, "graph autotune"); }
+    g->variant = ms[1] < ms[0] ? 1 : 0;
+    if (report && report_len) {
+        std::snprintf(report, report_len, "{\"push_ms_per_step\": %.6f, \"pull_ms_per_step\": %.6f, \"variant\": %d}",
+                      ms[0] / 6, ms[1] / 6, g->variant);
+    }
+    return QW_OK;
+}
+
+qw_status qw_gwalk_synchronize(qw_gwalk *g) {
+    if (!g) return QW_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    return e == cudaSuccess ? QW_OK : gcuda(g, e, "graph synchronize");
+}
+
+}  // extern "C"

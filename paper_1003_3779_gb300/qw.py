@@ -12,6 +12,7 @@ U = S (I (x) C) on the cycle (coin dim 2) or torus (coin dim 4).
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 
 import numpy as np
@@ -81,6 +82,21 @@ def lib():
         "qw_batch_set_cta_walks": (I, [P, I]),
         "qw_batch_cta_walks": (I, [P]),
         "qw_batch_get_plan_ex": (I, [P, P, P, P]),
+        "qw_graph_arcs": (I, [I64, I64, P, P, P]),
+        "qw_gwalk_create": (I, [I64, P, P, I, P, P]),
+        "qw_gwalk_destroy": (I, [P]),
+        "qw_gwalk_set_coin": (I, [P, I, P, I]),
+        "qw_gwalk_set_state": (I, [P, P, I, I]),
+        "qw_gwalk_get_state": (I, [P, P, I, I]),
+        "qw_gwalk_step": (I, [P, I64]),
+        "qw_gwalk_step_adjoint": (I, [P, I64]),
+        "qw_gwalk_probabilities": (I, [P, P, I, I, P]),
+        "qw_gwalk_set_variant": (I, [P, I]),
+        "qw_gwalk_get_variant": (I, [P, P]),
+        "qw_gwalk_autotune": (I, [P, ctypes.c_char_p, S]),
+        "qw_gwalk_synchronize": (I, [P]),
+        "qw_gwalk_narcs": (I64, [P]),
+        "qw_gwalk_last_error": (ctypes.c_char_p, [P]),
         "qw_status_string": (ctypes.c_char_p, [I]),
         "qw_last_error": (ctypes.c_char_p, [P]),
         "qw_batch_last_error": (ctypes.c_char_p, [P]),
@@ -108,7 +124,8 @@ def _check(st, handle=None, batch=False):
     L = lib()
     msg = L.qw_status_string(st).decode()
     if handle is not None:
-        detail = (L.qw_batch_last_error(handle) if batch else L.qw_last_error(handle)).decode()
+        err = {False: L.qw_last_error, True: L.qw_batch_last_error, "graph": L.qw_gwalk_last_error}[batch]
+        detail = err(handle).decode()
         if detail:
             msg = f"{msg}: {detail}"
     raise QWError(st, msg)
@@ -504,3 +521,114 @@ def _region_mass_function():
 def region_mass(phi, walk, base, psi0, rect, T, K=64):
     """Differentiable region mass (see RegionMass)."""
     return _region_mass_function().apply(phi, walk, base, psi0, rect, T, K)
+
+
+# ---------------------------------------------------------------- graphs
+GCOIN_GROVER, GCOIN_UNIFORM, GCOIN_PER_VERTEX = 0, 1, 2
+
+
+def graph_arcs(nvert, edges):
+    """Arc form (off, partner) of an edge list, built by the library
+    (qw_graph_arcs): vertex v's arcs are off[v] .. off[v+1]-1 in the order its
+    edge ends appear, partner[a] the arc at the other end of a's edge."""
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int64).reshape(-1, 2))
+    off = np.empty(int(nvert) + 1, dtype=np.int64)
+    partner = np.empty(2 * len(e), dtype=np.int64)
+    _check(lib().qw_graph_arcs(int(nvert), len(e), _ptr(e), _ptr(off), _ptr(partner)))
+    return off, partner
+
+
+class GraphWalk:
+    """The walk on a general graph (Sec. 2.1) in arc form: one amplitude per
+    (vertex, edge end); ``prec`` "f64" or "f32".  The default coin is Grover."""
+
+    def __init__(self, off, partner, prec="f32", stream=None):
+        off = np.ascontiguousarray(off, dtype=np.int64)
+        partner = np.ascontiguousarray(partner, dtype=np.int64)
+        self.nvert = len(off) - 1
+        self.narcs = int(off[-1])
+        self.deg = np.diff(off)
+        self.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        h = ctypes.c_void_p()
+        _check(lib().qw_gwalk_create(self.nvert, _ptr(off), _ptr(partner), self.prec,
+                                     stream if stream is not None else _stream(), ctypes.byref(h)))
+        self.h = h
+
+    def _ck(self, st):
+        _check(st, self.h, batch="graph")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qw_gwalk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_coin(self, coins=None):
+        """None: Grover; one d x d matrix (regular graph); or a list of
+        per-vertex d(v) x d(v) matrices; or a flat complex array (host or
+        device) of the concatenated per-vertex matrices."""
+        if coins is None:
+            self._ck(lib().qw_gwalk_set_coin(self.h, GCOIN_GROVER, None, 0))
+            return self
+        if isinstance(coins, np.ndarray) and coins.ndim == 2:
+            c = np.ascontiguousarray(coins, dtype=np.complex128)
+            self._ck(lib().qw_gwalk_set_coin(self.h, GCOIN_UNIFORM, _ptr(c), 0))
+            return self
+        if isinstance(coins, (list, tuple)):
+            parts = [np.asarray(m, dtype=np.complex128).ravel() for m in coins]
+            coins = np.concatenate(parts) if parts else np.zeros(0, np.complex128)
+        if isinstance(coins, np.ndarray):
+            coins = np.ascontiguousarray(coins, dtype=np.complex128)
+            if coins.size == 0:
+                coins = np.zeros(1, np.complex128)
+        self._ck(lib().qw_gwalk_set_coin(self.h, GCOIN_PER_VERTEX, _ptr(coins), _on_device(coins)))
+        return self
+
+    def set_state(self, amp):
+        if isinstance(amp, np.ndarray):
+            amp = np.ascontiguousarray(amp if amp.dtype in (np.complex64, np.complex128) else amp.astype(np.complex128))
+        self._ck(lib().qw_gwalk_set_state(self.h, _ptr(amp), _cdtype(amp), _on_device(amp)))
+        return self
+
+    def state(self, dtype=np.complex128, out=None):
+        if out is None:
+            out = np.empty(self.narcs, dtype=dtype)
+        self._ck(lib().qw_gwalk_get_state(self.h, _ptr(out), _cdtype(out), _on_device(out)))
+        return out
+
+    def step(self, T):
+        self._ck(lib().qw_gwalk_step(self.h, int(T)))
+        return self
+
+    def step_adjoint(self, T):
+        self._ck(lib().qw_gwalk_step_adjoint(self.h, int(T)))
+        return self
+
+    def probabilities(self, dtype=np.float64):
+        P = np.empty(self.nvert, dtype=dtype)
+        norm = ctypes.c_double(0.0)
+        self._ck(lib().qw_gwalk_probabilities(self.h, _ptr(P), R32 if P.dtype == np.float32 else R64, 0,
+                                              ctypes.byref(norm)))
+        return P, norm.value
+
+    def set_variant(self, v):
+        self._ck(lib().qw_gwalk_set_variant(self.h, int(v)))
+        return self
+
+    def variant(self):
+        v = ctypes.c_int(0)
+        self._ck(lib().qw_gwalk_get_variant(self.h, ctypes.byref(v)))
+        return v.value
+
+    def autotune(self):
+        buf = ctypes.create_string_buffer(512)
+        self._ck(lib().qw_gwalk_autotune(self.h, buf, 512))
+        return json.loads(buf.value.decode())
+
+    def synchronize(self):
+        self._ck(lib().qw_gwalk_synchronize(self.h))

@@ -79,3 +79,40 @@ def test_null_handles_are_rejected(qwlib):
     assert L.qw_destroy(None) == qwlib.QW_OK
     assert L.qw_create(1, None, 2, 0, 0, 1, None, None) == qwlib.QW_EINVAL
     assert L.qw_last_error(None) == b"null handle"
+
+
+def test_graph_arcs_match_the_oracle_bitwise(qwlib):
+    """qw_graph_arcs (host code of the library) and the oracle's own arc builder
+    give the same arc form: integer work, compared exactly."""
+    import oracle
+    from paper_1003_3779_gb300 import inputs
+    for nvert, edges in [(3, [(0, 1), (1, 1), (2, 0)]),
+                         (7, [(i, (i * 3 + 1) % 7) for i in range(7)] + [(2, 2), (5, 6), (5, 6)]),
+                         (2000, inputs.chung_lu_edges(2000, 5, 2.3, seed=9)),
+                         (4, np.zeros((0, 2), dtype=np.int64))]:
+        off, partner = qwlib.graph_arcs(nvert, edges)
+        off_o, partner_o = oracle.graph_arcs(nvert, edges)
+        assert np.array_equal(off, off_o) and np.array_equal(partner, partner_o)
+    with pytest.raises(qwlib.QWError):
+        qwlib.graph_arcs(3, [(0, 3)])
+
+
+def test_graph_walk_create_rejects_bad_graphs_without_a_gpu(qwlib):
+    L = qwlib.lib()
+
+    def create(off, partner, prec=1):
+        off = np.asarray(off, dtype=np.int64)
+        partner = np.asarray(partner, dtype=np.int64)
+        h = ctypes.c_void_p(123)
+        st = L.qw_gwalk_create(len(off) - 1, off.ctypes.data_as(ctypes.c_void_p),
+                               partner.ctypes.data_as(ctypes.c_void_p), prec, None, ctypes.byref(h))
+        return st, h.value
+
+    assert create([0, 2, 4], [1, 2, 3, 0]) == (qwlib.QW_EINVAL, None)      # not an involution
+    assert create([0, 2, 4], [1, 0, 3, 4]) == (qwlib.QW_EINVAL, None)      # out of range
+    assert create([0, 3, 2], [1, 0]) == (qwlib.QW_EINVAL, None)            # off decreasing
+    assert create([1, 3], [1, 0]) == (qwlib.QW_EINVAL, None)               # off[0] != 0
+    assert create([0, 2], [1, 0], prec=2) == (qwlib.QW_EUNSUPPORTED, None)  # bf16 storage
+    assert L.qw_gwalk_step(None, 1) == qwlib.QW_EINVAL
+    assert L.qw_gwalk_destroy(None) == qwlib.QW_OK
+    assert L.qw_gwalk_narcs(None) == -1
