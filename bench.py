@@ -22,6 +22,7 @@ data path ("weak" scaling); a barrier and a max-over-ranks of the time only.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -208,6 +209,38 @@ def ncu_traffic(kernel="k_step1d_sweep", tile=None):
     if tile is not None and (not t or int(t.group(1)) != tile):
         return None
     return float(b.group(1))
+
+
+def graph_timing(qw, _in, make, stream, hbm_gbs, steps=20):
+    """One graph workload: build it, autotune the kernel form, time `steps` walk
+    steps with CUDA events on the launching stream, check the norm."""
+    import torch
+    t0 = time.perf_counter()
+    off, partner = make()
+    A = int(off[-1])
+    gw = qw.GraphWalk(off, partner, prec="f32", stream=ctypes.c_void_p(stream.cuda_stream))
+    del partner
+    gw.set_state(torch.from_numpy(_in.random_state((A,), seed=6, dtype=np.complex64)).cuda())
+    tune = gw.autotune()
+    setup_s = time.perf_counter() - t0
+    gw.step(3)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    gw.step(steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b) / 1e3 / steps
+    _, norm = gw.probabilities()
+    gw.close()
+    # algorithmic bytes of one step: read psi (8 B), write psi' (8 B), read the
+    # partner index (4 B) per arc; the two-pass forms move about twice that
+    alg = 20.0 * A
+    return {"arc_updates_per_s": A / t, "ms_per_step": t * 1e3, "arcs": A, "vertices": len(off) - 1,
+            "variant": tune["variant"], "autotune": tune, "steps": steps, "setup_s": setup_s,
+            "hbm_view": {"algorithmic_bytes_per_arc_step": 20, "achieved_gbs": alg / t / 1e9,
+                         "peak_gbs": hbm_gbs, "frac": alg / t / 1e9 / hbm_gbs},
+            "norm_err": abs(norm - 1.0)}
 
 
 def run_gpu(args, rank, world, local):
@@ -436,7 +469,16 @@ def run_gpu(args, rank, world, local):
                     "note": "forward T steps with checkpoints + T adjoint steps, host wall clock"}
         wg.close()
 
-    # accuracy and the other precision forms on the same input (rank 0 only)
+    # the walk on a general graph (Sec. 2.1), Grover coin, FP32: a random 4-regular
+    # multigraph (configuration model) with 2^26 vertices and the 8192^2 torus as a
+    # graph, both 2^28 arcs; the autotuner picks the kernel form
+    graph_leg = {}
+    if rank == 0 and not args.skip_forms:
+        from paper_1003_3779_gb300 import inputs as _in
+        for gname, make in (("random_4_regular_2e26", lambda: _in.random_regular_arcs(1 << 26, 4, seed=5)),
+                            ("torus_8192_as_graph", lambda: _in.lattice_graph_arcs(8192, 8192))):
+            graph_leg[gname] = graph_timing(qw, _in, make, stream, hbm_gbs)
+
     forms, accuracy = {}, {}
     if rank == 0 and not args.skip_forms:
         qw.qw_set_state(w.h, dev0)
@@ -482,7 +524,7 @@ def run_gpu(args, rank, world, local):
         "value": value, "elapsed": tmax, "norm": norm, "roofline": roof, "roofline_k1": roof_k1,
         "forms": forms, "accuracy": accuracy, "e2e": e2e, "clocks": clk.summary(), "tune": tune,
         "K": K, "tile": tile, "launches": args.steps * (launches_step + 2), "dist": dist,
-        "torus": torus, "batch": batch, "grad": grad_leg,
+        "torus": torus, "batch": batch, "grad": grad_leg, "graph": graph_leg,
     }
 
 
@@ -495,6 +537,28 @@ def run_case(args):
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)
     out = {"case": args.case}
+    if args.case == "graph":
+        # random 4-regular multigraph of --n-sites vertices, Grover coin, FP32;
+        # --plan: the kernel form (default: autotuned)
+        nv = args.n_sites if args.n_sites != N_SITES else 1 << 23
+        off, partner = _in.random_regular_arcs(nv, 4, seed=5)
+        A = int(off[-1])
+        gw = qw.GraphWalk(off, partner, prec="f32")
+        gw.set_state(torch.from_numpy(_in.random_state((A,), seed=6, dtype=np.complex64)).cuda())
+        if args.plan:
+            gw.set_variant(int(args.plan))
+        else:
+            out["autotune"] = gw.autotune()
+        gw.step(2)
+        a, b = ev(), ev()
+        a.record(stream)
+        gw.step(args.steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out.update(vertices=nv, arcs=A, variant=gw.variant(), ms_per_step=a.elapsed_time(b) / args.steps)
+        gw.close()
+        print(json.dumps(out))
+        return
     if args.case == "torus":
         L = args.n_sites
         g = torch.Generator(device="cuda").manual_seed(2)
@@ -549,7 +613,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--n-sites", type=int, default=N_SITES,
                     help="cycle length (default 2^27; smaller only for profiling captures)")
-    ap.add_argument("--case", default="", choices=["", "torus", "batch", "grad"],
+    ap.add_argument("--case", default="", choices=["", "torus", "batch", "grad", "graph"],
                     help="run a small named workload for kernel captures instead of the benchmark")
     ap.add_argument("--walks", type=int, default=4096, help="walks of the batch case")
     ap.add_argument("--plan", default="",
@@ -597,7 +661,7 @@ def main():
         "clocks": r["clocks"], "e2e": r["e2e"], "gpu_launches": r["launches"],
         "roofline": r["roofline"], "roofline_k1": r["roofline_k1"], "cpu_baseline": cpu,
         "accuracy": r["accuracy"], "forms": r["forms"], "torus_8192": r["torus"],
-        "batch_4096": r["batch"], "region_grad_1024": r["grad"],
+        "batch_4096": r["batch"], "region_grad_1024": r["grad"], "graph": r["graph"],
         "norm": r["norm"], "autotune": r["tune"],
     }
     print(json.dumps(out))

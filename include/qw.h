@@ -302,12 +302,22 @@ qw_status qw_gwalk_probabilities(qw_gwalk *g, void *P_out, qw_rdtype pdtype, int
 
 /* Form of the forward step: 0 push (each arc's thread reads its own vertex and
  * writes the partner arc), 1 pull (reads the partner's vertex, writes its own
- * arc); -1 restores the default (push).  Both give the same bits. */
+ * arc), 2 and 3 two passes through L2-sized destination buckets (the first
+ * computes the coin and writes bucket runs, the second permutes within one
+ * L2-resident window by scattered writes (2) or gathered reads (3)); -1
+ * restores the default (push).  Every form gives the same bits.  Forms 2 and 3
+ * build tables on first use (host work O(arcs); device memory 10 bytes per arc
+ * plus one more state buffer). */
 qw_status qw_gwalk_set_variant(qw_gwalk *g, int variant);
+
+/* Output bytes each destination bucket of forms 2 and 3 covers (default
+ * 16 MiB, an eighth of L2); the tables are rebuilt.  QW_EINVAL below one
+ * amplitude. */
+qw_status qw_gwalk_set_window(qw_gwalk *g, size_t bytes);
 qw_status qw_gwalk_get_variant(const qw_gwalk *g, int *variant);
 
-/* Time both forms on the current state (which is saved and restored), keep
- * the faster, and write a JSON report. */
+/* Time the forms on the current state (which is saved and restored), keep
+ * the fastest, and write a JSON report. */
 qw_status qw_gwalk_autotune(qw_gwalk *g, char *report, size_t report_len);
 
 qw_status qw_gwalk_synchronize(qw_gwalk *g);

@@ -21,8 +21,17 @@
 //   pull (variant 1): thread a reads the vertex of partner[a] (a scattered
 //     read of that vertex's arcs) and writes psi'(a) (coalesced).
 // On a graph whose arcs are ordered with locality (lattices) both stream; on a
-// random graph the scattered side costs whole 32-byte sectors, and which side
-// is cheaper is measured (qw_gwalk_autotune).
+// random graph the scattered side costs whole 32-byte sectors at random DRAM
+// addresses.  Two more forms route the permutation through L2 instead, in two
+// passes, as a radix-sort scatter does:
+//   pass 1 computes phi with coalesced reads and writes it into destination
+//     buckets (each bucket covers GR_WINDOW bytes of the output): a tile of
+//     GR_TILE arcs is ordered by bucket in shared memory first, so the writes
+//     leave as contiguous runs;
+//   pass 2 moves each bucket to its final places, which all lie in one window
+//     small enough to stay in L2: scattered writes (variant 2) or gathered
+//     reads (variant 3) hit L2, and DRAM sees whole lines.
+// Which form is fastest for a graph is measured (qw_gwalk_autotune).
 //
 // Regular graphs of degree 2 or 4 find an arc's vertex by division; others
 // read it from a per-arc vertex index.  The Grover coin (2/d) J - I needs the
@@ -43,6 +52,8 @@ namespace qw {
 static constexpr int GR_THREADS = 256;
 static constexpr int GR_HEAVY = 32;
 static constexpr int GR_RED_BLOCKS = 152 * 4;
+static constexpr int GR_TILE = 1024;                       // arcs per block of the bucketing pass
+static constexpr size_t GR_WINDOW = size_t(16) << 20;      // output bytes per bucket
 
 template <class R>
 struct GraphArgs {
@@ -94,6 +105,46 @@ __device__ __forceinline__ Cx<R> coin_row(const GraphArgs<R> &g, const Cx<R> *__
     }
 }
 
+// Row i of the coin at v applied to amplitudes already in registers (regular
+// graphs of degree DR, forward step).
+template <int MODE, int DR, class R>
+__device__ __forceinline__ Cx<R> coin_row_reg(const GraphArgs<R> &g, const Cx<R> (&x)[DR], int v, int i) {
+    if constexpr (MODE == QW_GCOIN_GROVER) {
+        Cx<R> s{R(0), R(0)};
+#pragma unroll
+        for (int j = 0; j < DR; ++j) s = cadd(s, x[j]);
+        return csub(rmul(R(2) / R(DR), s), x[i]);
+    } else {
+        const Cx<R> *C = MODE == QW_GCOIN_UNIFORM ? g.coins : g.coins + g.coff[v];
+        Cx<R> acc{R(0), R(0)};
+#pragma unroll
+        for (int j = 0; j < DR; ++j) acc = cfma(C[i * DR + j], x[j], acc);
+        return acc;
+    }
+}
+
+// the DR amplitudes of vertex v with 16-byte loads (the vertex starts on a
+// multiple of DR * sizeof(Cx<R>) >= 16 bytes)
+template <int DR, class R>
+__device__ __forceinline__ void load_vertex(const Cx<R> *__restrict__ in, int v, Cx<R> (&x)[DR]) {
+    if constexpr (sizeof(R) == 4) {
+        const float4 *p = reinterpret_cast<const float4 *>(in + v * DR);
+#pragma unroll
+        for (int j = 0; j < DR / 2; ++j) {
+            const float4 q = p[j];
+            x[2 * j] = Cx<R>{q.x, q.y};
+            x[2 * j + 1] = Cx<R>{q.z, q.w};
+        }
+    } else {
+        const double2 *p = reinterpret_cast<const double2 *>(in + v * DR);
+#pragma unroll
+        for (int j = 0; j < DR; ++j) {
+            const double2 q = p[j];
+            x[j] = Cx<R>{q.x, q.y};
+        }
+    }
+}
+
 // forward, push: psi'(partner[a]) = row i of C_v applied to psi at v
 template <class R, int MODE, int DR>
 __global__ void __launch_bounds__(GR_THREADS)
@@ -126,6 +177,93 @@ k_graph_adjoint(GraphArgs<R> g, const Cx<R> *__restrict__ in, Cx<R> *__restrict_
     int v, o, d;
     vertex_of<DR>(g, a, v, o, d);
     out[a] = coin_row<MODE, DR, 1>(g, in, v, o, d, a - o);
+}
+
+// two-pass forward, pass 1: phi of the tile's arcs, ordered by destination
+// bucket in shared memory (lpos: the arc's place in that order), then written
+// to its bucket slots (gsl: the slot of each place), contiguous per bucket
+template <class R, int MODE, int DR>
+__global__ void __launch_bounds__(GR_THREADS)
+k_graph_bucket(GraphArgs<R> g, const Cx<R> *__restrict__ in, const unsigned short *__restrict__ lpos,
+               const int *__restrict__ gsl, Cx<R> *__restrict__ tmp) {
+    __shared__ Cx<R> sm[GR_TILE];
+    const int base = blockIdx.x * GR_TILE;
+    const int n = min(GR_TILE, g.A - base);
+    if constexpr (DR > 0) {
+        // a thread per vertex: one vector load of its DR amplitudes (GR_TILE is
+        // a multiple of DR, so tiles hold whole vertices)
+        for (int vv = threadIdx.x; vv < n / DR; vv += GR_THREADS) {
+            const int v = base / DR + vv;
+            Cx<R> x[DR];
+            load_vertex<DR>(in, v, x);
+#pragma unroll
+            for (int i = 0; i < DR; ++i) sm[lpos[v * DR + i]] = coin_row_reg<MODE, DR>(g, x, v, i);
+        }
+    } else {
+        for (int i = threadIdx.x; i < n; i += GR_THREADS) {
+            const int a = base + i;
+            int v, o, d;
+            vertex_of<DR>(g, a, v, o, d);
+            sm[lpos[a]] = coin_row<MODE, DR, 0>(g, in, v, o, d, a - o);
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += GR_THREADS) tmp[__ldcs(gsl + base + j)] = sm[j];
+}
+
+// pass 2, scatter form: slot s of the bucketed phi goes to arc dst[s]
+template <class R>
+__global__ void __launch_bounds__(GR_THREADS)
+k_graph_scatter(int A, const int *__restrict__ dst, const Cx<R> *__restrict__ tmp, Cx<R> *__restrict__ out) {
+    const int s = blockIdx.x * GR_THREADS + threadIdx.x;
+    if (s < A) out[__ldg(dst + s)] = tmp[s];
+}
+
+// pass 2, gather form: arc a takes bucketed slot srcs[a].  Bucket w holds
+// exactly the values bound for the arcs of window w, so its slots are the same
+// index range; each thread asks L2 for the slot one window ahead of its arc
+// (pf), so that the next window's bucket is read from DRAM in order while this
+// window's random reads hit L2.  The index and output streams are marked
+// evict-first to leave L2 to the buckets.
+static constexpr int GR_GATHER = 8;   // arcs per thread of the gather pass (loads in flight)
+
+// L2-only load (the random reads of the gather pass gain nothing from L1)
+__device__ __forceinline__ Cx<float> ldcg(const Cx<float> *p) {
+    const float2 q = __ldcg(reinterpret_cast<const float2 *>(p));
+    return Cx<float>{q.x, q.y};
+}
+__device__ __forceinline__ Cx<double> ldcg(const Cx<double> *p) {
+    const double2 q = __ldcg(reinterpret_cast<const double2 *>(p));
+    return Cx<double>{q.x, q.y};
+}
+
+template <class R>
+__global__ void __launch_bounds__(GR_THREADS)
+k_graph_gather(int A, const int *__restrict__ srcs, const Cx<R> *__restrict__ tmp, Cx<R> *__restrict__ out, int pf) {
+    const int a0 = blockIdx.x * (GR_THREADS * GR_GATHER) + threadIdx.x;
+    int sl[GR_GATHER];
+    Cx<R> v[GR_GATHER];
+#pragma unroll
+    for (int k = 0; k < GR_GATHER; ++k) {
+        const int a = a0 + k * GR_THREADS;
+        if (a < A) {
+            if (pf > 0 && a < A - pf) asm volatile("prefetch.global.L2 [%0];" ::"l"(tmp + a + pf));
+            sl[k] = __ldcs(srcs + a);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < GR_GATHER; ++k)
+        if (a0 + k * GR_THREADS < A) v[k] = ldcg(tmp + sl[k]);
+#pragma unroll
+    for (int k = 0; k < GR_GATHER; ++k) {
+        const int a = a0 + k * GR_THREADS;
+        if (a >= A) continue;
+        if constexpr (sizeof(R) == 4) {
+            __stcs(reinterpret_cast<float2 *>(out + a), make_float2(v[k].re, v[k].im));
+        } else {
+            __stcs(reinterpret_cast<double2 *>(out + a), make_double2(v[k].re, v[k].im));
+        }
+    }
 }
 
 // Grover pre-pass: the amplitude sum of each heavy vertex (of psi, or of S psi
@@ -225,6 +363,13 @@ struct qw_gwalk {
     void *staging = nullptr;
     size_t staging_bytes = 0;
     int variant = -1;             // -1: default (push)
+    // two-pass forms: bucket order of each tile, bucket slot of each tile
+    // place, final arc of each slot (scatter) / slot of each arc (gather)
+    unsigned short *lpos_dev = nullptr;
+    int *gsl_dev = nullptr, *dst_dev = nullptr, *slot_dev = nullptr;
+    void *tmp_dev = nullptr;
+    size_t window = GR_WINDOW;    // output bytes per bucket
+    int window_arcs = 0;          // arcs per bucket of the built tables
     std::string err;
 };
 
@@ -275,6 +420,21 @@ cudaError_t launch_mode_dr(const GraphArgs<R> &a, int kernel, const Cx<R> *in, C
     return cudaGetLastError();
 }
 
+template <class R, int MODE, int DR>
+cudaError_t launch_bucket_dr(const GraphArgs<R> &a, const qw_gwalk *g, const Cx<R> *in) {
+    const unsigned tiles = (unsigned)((a.A + GR_TILE - 1) / GR_TILE);
+    k_graph_bucket<R, MODE, DR><<<tiles, GR_THREADS, 0, g->stream>>>(a, in, g->lpos_dev, g->gsl_dev,
+                                                                       static_cast<Cx<R> *>(g->tmp_dev));
+    return cudaGetLastError();
+}
+
+template <class R, int MODE>
+cudaError_t launch_bucket(const qw_gwalk *g, const GraphArgs<R> &a, const Cx<R> *in) {
+    if (g->dreg == 2) return launch_bucket_dr<R, MODE, 2>(a, g, in);
+    if (g->dreg == 4) return launch_bucket_dr<R, MODE, 4>(a, g, in);
+    return launch_bucket_dr<R, MODE, 0>(a, g, in);
+}
+
 template <class R, int MODE>
 cudaError_t launch_mode(const qw_gwalk *g, const GraphArgs<R> &a, int kernel, const Cx<R> *in, Cx<R> *out) {
     if (g->dreg == 2) return launch_mode_dr<R, MODE, 2>(a, kernel, in, out, g->stream);
@@ -297,6 +457,22 @@ cudaError_t graph_step(qw_gwalk *g, int kernel) {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    if (kernel >= 3) {   // two-pass forms
+        cudaError_t e;
+        switch (g->mode) {
+            case QW_GCOIN_GROVER: e = launch_bucket<R, QW_GCOIN_GROVER>(g, a, in); break;
+            case QW_GCOIN_UNIFORM: e = launch_bucket<R, QW_GCOIN_UNIFORM>(g, a, in); break;
+            default: e = launch_bucket<R, QW_GCOIN_PER_VERTEX>(g, a, in); break;
+        }
+        if (e != cudaSuccess) return e;
+        const unsigned blocks = (unsigned)((a.A + GR_THREADS - 1) / GR_THREADS);
+        const Cx<R> *tmp = static_cast<const Cx<R> *>(g->tmp_dev);
+        if (kernel == 3) k_graph_scatter<R><<<blocks, GR_THREADS, 0, g->stream>>>(a.A, g->dst_dev, tmp, out);
+        else
+            k_graph_gather<R><<<(unsigned)((a.A + GR_THREADS * GR_GATHER - 1) / (GR_THREADS * GR_GATHER)), GR_THREADS, 0,
+                                g->stream>>>(a.A, g->slot_dev, tmp, out, g->window_arcs);
+        return cudaGetLastError();
+    }
     switch (g->mode) {
         case QW_GCOIN_GROVER: return launch_mode<R, QW_GCOIN_GROVER>(g, a, kernel, in, out);
         case QW_GCOIN_UNIFORM: return launch_mode<R, QW_GCOIN_UNIFORM>(g, a, kernel, in, out);
@@ -304,9 +480,73 @@ cudaError_t graph_step(qw_gwalk *g, int kernel) {
     }
 }
 
+// The tables of the two-pass forms, built on the host once per graph: the
+// destination bucket of arc a is partner[a] / W (W arcs per GR_WINDOW bytes);
+// slots are bucket-major, then tile, then arc order; within a tile the arcs
+// are ordered by bucket (a counting sort), so each tile's run for a bucket is
+// contiguous both in shared memory and in the slot array.
+qw_status ensure_two_pass(qw_gwalk *g) {
+    if (g->tmp_dev) return QW_OK;
+    const int A = g->A;
+    std::vector<int> partner((size_t)A);
+    if (A) {
+        cudaError_t e = cudaMemcpyAsync(partner.data(), g->partner_dev, sizeof(int) * (size_t)A, cudaMemcpyDeviceToHost,
+                                        g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) return gcuda(g, e, "two-pass tables");
+    }
+    const int64_t W = std::max<int64_t>(1, (int64_t)(g->window / amp_bytes(g)));
+    const int nb = (int)((A + W - 1) / W);
+    g->window_arcs = (int)std::min<int64_t>(W, A);
+    std::vector<int64_t> bstart((size_t)nb + 1, 0);
+    for (int a = 0; a < A; ++a) ++bstart[(size_t)(partner[(size_t)a] / W) + 1];
+    for (int b = 0; b < nb; ++b) bstart[(size_t)b + 1] += bstart[(size_t)b];
+    std::vector<int64_t> ptr(bstart.begin(), bstart.end() - 1);
+    std::vector<unsigned short> lpos((size_t)A);
+    std::vector<int> gsl((size_t)A), dst((size_t)A), slot((size_t)A);
+    std::vector<int> lcnt((size_t)nb), lstart((size_t)nb);
+    for (int base = 0; base < A; base += GR_TILE) {
+        const int n = std::min(GR_TILE, A - base);
+        std::fill(lcnt.begin(), lcnt.end(), 0);
+        for (int i = 0; i < n; ++i) ++lcnt[(size_t)(partner[(size_t)(base + i)] / W)];
+        int acc = 0;
+        for (int b = 0; b < nb; ++b) { lstart[(size_t)b] = acc; acc += lcnt[(size_t)b]; }
+        for (int i = 0; i < n; ++i) {
+            const int a = base + i;
+            const int b = (int)(partner[(size_t)a] / W);
+            const int place = lstart[(size_t)b]++;
+            const int s = (int)ptr[(size_t)b]++;
+            lpos[(size_t)a] = (unsigned short)place;
+            gsl[(size_t)(base + place)] = s;
+            dst[(size_t)s] = partner[(size_t)a];
+            slot[(size_t)partner[(size_t)a]] = s;
+        }
+    }
+    const size_t n4 = sizeof(int) * (size_t)std::max(A, 1);
+    cudaError_t e = dev_alloc((void **)&g->lpos_dev, sizeof(unsigned short) * (size_t)std::max(A, 1));
+    if (e == cudaSuccess) e = dev_alloc((void **)&g->gsl_dev, n4);
+    if (e == cudaSuccess) e = dev_alloc((void **)&g->dst_dev, n4);
+    if (e == cudaSuccess) e = dev_alloc((void **)&g->slot_dev, n4);
+    if (e == cudaSuccess) e = dev_alloc(&g->tmp_dev, (size_t)std::max(A, 1) * amp_bytes(g));
+    if (e == cudaSuccess && A) {
+        e = cudaMemcpyAsync(g->lpos_dev, lpos.data(), sizeof(unsigned short) * A, cudaMemcpyHostToDevice, g->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->gsl_dev, gsl.data(), sizeof(int) * (size_t)A, cudaMemcpyHostToDevice, g->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->dst_dev, dst.data(), sizeof(int) * (size_t)A, cudaMemcpyHostToDevice, g->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->slot_dev, slot.data(), sizeof(int) * (size_t)A, cudaMemcpyHostToDevice, g->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) {
+        for (void *p : {(void *)g->lpos_dev, (void *)g->gsl_dev, (void *)g->dst_dev, (void *)g->slot_dev, g->tmp_dev})
+            if (p) cudaFree(p);
+        g->lpos_dev = nullptr; g->gsl_dev = g->dst_dev = g->slot_dev = nullptr; g->tmp_dev = nullptr;
+        return gcuda(g, e, "two-pass tables");
+    }
+    return QW_OK;
+}
+
 qw_status run_graph(qw_gwalk *g, int64_t T, int adj) {
     if (T < 0) return gfail(g, QW_EINVAL, "T must be >= 0");
-    const int kernel = adj ? 2 : (g->variant == 1 ? 1 : 0);
+    const int kernel = adj ? 2 : (g->variant <= 0 ? 0 : (g->variant == 1 ? 1 : g->variant + 1));
     for (int64_t t = 0; t < T; ++t) {
         cudaError_t e = g->prec == QW_F64 ? graph_step<double>(g, kernel) : graph_step<float>(g, kernel);
         if (e != cudaSuccess) return gcuda(g, e, "graph step launch");
@@ -335,7 +575,8 @@ void free_all(qw_gwalk *g) {
     if (g->stream) cudaStreamSynchronize(g->stream);
     for (void *p : {(void *)g->off_dev, (void *)g->src_dev, (void *)g->partner_dev, g->buf[0], g->buf[1], g->coins_dev,
                     (void *)g->coff_dev, (void *)g->heavy_dev, g->vsum_dev, (void *)g->partials, (void *)g->norm_dev,
-                    g->p_dev, g->staging})
+                    g->p_dev, g->staging, (void *)g->lpos_dev, (void *)g->gsl_dev, (void *)g->dst_dev,
+                    (void *)g->slot_dev, g->tmp_dev})
         if (p) cudaFree(p);
 }
 
@@ -610,14 +851,32 @@ qw_status qw_gwalk_probabilities(qw_gwalk *g, void *P_out, qw_rdtype pdtype, int
 
 qw_status qw_gwalk_set_variant(qw_gwalk *g, int variant) {
     if (!g) return QW_EINVAL;
-    if (variant < -1 || variant > 1) return gfail(g, QW_EINVAL, "variant must be -1 (default), 0 (push) or 1 (pull)");
+    if (variant < -1 || variant > 3)
+        return gfail(g, QW_EINVAL, "variant must be -1 (default), 0 (push), 1 (pull), 2 or 3 (two-pass)");
+    if (variant >= 2) {
+        qw_status st = ensure_two_pass(g);
+        if (st != QW_OK) return st;
+    }
     g->variant = variant;
+    return QW_OK;
+}
+
+qw_status qw_gwalk_set_window(qw_gwalk *g, size_t bytes) {
+    if (!g) return QW_EINVAL;
+    if (bytes < amp_bytes(g)) return gfail(g, QW_EINVAL, "the window must hold at least one amplitude");
+    if (bytes == g->window) return QW_OK;
+    cudaStreamSynchronize(g->stream);
+    for (void *p : {(void *)g->lpos_dev, (void *)g->gsl_dev, (void *)g->dst_dev, (void *)g->slot_dev, g->tmp_dev})
+        if (p) cudaFree(p);
+    g->lpos_dev = nullptr; g->gsl_dev = g->dst_dev = g->slot_dev = nullptr; g->tmp_dev = nullptr;
+    g->window = bytes;
+    if (g->variant >= 2) return ensure_two_pass(g);
     return QW_OK;
 }
 
 qw_status qw_gwalk_get_variant(const qw_gwalk *g, int *variant) {
     if (!g || !variant) return QW_EINVAL;
-    *variant = g->variant == 1 ? 1 : 0;
+    *variant = g->variant < 0 ? 0 : g->variant;
     return QW_OK;
 }
 
@@ -632,9 +891,11 @@ qw_status qw_gwalk_autotune(qw_gwalk *g, char *report, size_t report_len) {
     qw_status st = ensure_staging(g, std::max<size_t>(sb, 16));
     if (st != QW_OK) return st;
     cudaError_t e = cudaMemcpyAsync(g->staging, g->buf[g->cur], sb, cudaMemcpyDeviceToDevice, g->stream);
-    float ms[2] = {0.f, 0.f};
+    float ms[4] = {0.f, 0.f, 0.f, 0.f};
     const int saved = g->variant;
-    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+    // the two-pass forms only where their tables fit (they are built once)
+    const int nvar = (e == cudaSuccess && ensure_two_pass(g) == QW_OK) ? 4 : 2;
+    for (int v = 0; v < nvar && e == cudaSuccess; ++v) {
         g->variant = v;
         if (run_graph(g, 2, 0) != QW_OK) { e = cudaErrorLaunchFailure; break; }
         cudaEventRecord(e0, g->stream);
@@ -647,10 +908,15 @@ qw_status qw_gwalk_autotune(qw_gwalk *g, char *report, size_t report_len) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) { g->variant = saved; return gcuda(g, e, "graph autotune"); }
-    g->variant = ms[1] < ms[0] ? 1 : 0;
+    int best = 0;
+    for (int v = 1; v < nvar; ++v)
+        if (ms[v] < ms[best]) best = v;
+    g->variant = best;
     if (report && report_len) {
-        std::snprintf(report, report_len, "{\"push_ms_per_step\": %.6f, \"pull_ms_per_step\": %.6f, \"variant\": %d}",
-                      ms[0] / 6, ms[1] / 6, g->variant);
+        std::snprintf(report, report_len,
+                      "{\"push_ms_per_step\": %.6f, \"pull_ms_per_step\": %.6f, \"two_pass_scatter_ms_per_step\": %.6f, "
+                      "\"two_pass_gather_ms_per_step\": %.6f, \"variant\": %d}",
+                      ms[0] / 6, ms[1] / 6, nvar > 2 ? ms[2] / 6 : -1.0, nvar > 2 ? ms[3] / 6 : -1.0, g->variant);
     }
     return QW_OK;
 }

@@ -93,6 +93,7 @@ def lib():
         "qw_gwalk_probabilities": (I, [P, P, I, I, P]),
         "qw_gwalk_set_variant": (I, [P, I]),
         "qw_gwalk_get_variant": (I, [P, P]),
+        "qw_gwalk_set_window": (I, [P, S]),
         "qw_gwalk_autotune": (I, [P, ctypes.c_char_p, S]),
         "qw_gwalk_synchronize": (I, [P]),
         "qw_gwalk_narcs": (I64, [P]),
@@ -618,6 +619,11 @@ class GraphWalk:
 
     def set_variant(self, v):
         self._ck(lib().qw_gwalk_set_variant(self.h, int(v)))
+        return self
+
+    def set_window(self, nbytes):
+        """Output bytes per destination bucket of the two-pass forms."""
+        self._ck(lib().qw_gwalk_set_window(self.h, int(nbytes)))
         return self
 
     def variant(self):

@@ -60,7 +60,7 @@ def coins_for(kind, off, rng):
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("name", GRAPHS)
 @pytest.mark.parametrize("coin", ["grover", "uniform", "per_vertex"])
-@pytest.mark.parametrize("form", ["push", "pull", "adjoint"])
+@pytest.mark.parametrize("form", ["push", "pull", "scatter2", "gather2", "adjoint"])
 def test_graph_walk_against_oracle(qw, prec, name, coin, form):
     off, partner = graph(name)
     deg = np.diff(off)
@@ -73,7 +73,9 @@ def test_graph_walk_against_oracle(qw, prec, name, coin, form):
     want = oracle.graph_evolve(off, partner, psi0, T, coins=C, adjoint=form == "adjoint")
     w = qw.GraphWalk(off, partner, prec=prec).set_coin(C).set_state(psi0)
     if form != "adjoint":
-        w.set_variant(0 if form == "push" else 1)
+        # the two-pass forms with windows of 40 amplitudes: many buckets, ragged ones
+        w.set_window(40 * (16 if prec == "f64" else 8))
+        w.set_variant(["push", "pull", "scatter2", "gather2"].index(form))
         w.step(T)
     else:
         w.step_adjoint(T)
@@ -87,17 +89,21 @@ def test_graph_walk_against_oracle(qw, prec, name, coin, form):
 
 
 @pytest.mark.parametrize("name", ["regular4", "chung_lu", "torus"])
-def test_push_and_pull_agree_bitwise(qw, name):
-    """Both forms evaluate the same expression per arc: identical bits."""
+@pytest.mark.parametrize("window", [8 * 1000, 8 * 4096, 1 << 25])
+def test_all_forms_agree_bitwise(qw, name, window):
+    """Every forward form evaluates the same expression per arc: identical bits,
+    whatever the bucket window of the two-pass forms."""
     off, partner = graph(name)
     psi0 = inputs.random_state((int(off[-1]),), seed=42).astype(np.complex64)
     out = []
-    for v in (0, 1):
-        w = qw.GraphWalk(off, partner, prec="f32").set_state(psi0).set_variant(v)
+    for v in range(4):
+        w = qw.GraphWalk(off, partner, prec="f32").set_state(psi0).set_window(window).set_variant(v)
         w.step(21)
+        assert w.variant() == v
         out.append(w.state(dtype=np.complex64))
         w.close()
-    assert np.array_equal(out[0], out[1])
+    for o in out[1:]:
+        assert np.array_equal(out[0], o)
 
 
 @pytest.mark.parametrize("dims", [(64,), (40, 24), (3, 5)])
@@ -165,7 +171,9 @@ def test_graph_edge_cases(qw):
     with pytest.raises(qw.QWError):
         w.set_coin(np.eye(2))
     with pytest.raises(qw.QWError):
-        w.set_variant(2)
+        w.set_variant(4)
+    with pytest.raises(qw.QWError):
+        w.set_window(4)
     w.close()
 
 
@@ -174,6 +182,7 @@ def test_autotune_keeps_the_state(qw):
     psi0 = inputs.random_state((int(off[-1]),), seed=45).astype(np.complex64)
     w = qw.GraphWalk(off, partner, prec="f32").set_state(psi0)
     rep = w.autotune()
-    assert rep["variant"] in (0, 1) and rep["push_ms_per_step"] > 0
+    assert rep["variant"] in (0, 1, 2, 3) and rep["push_ms_per_step"] > 0
+    assert rep["two_pass_gather_ms_per_step"] > 0
     assert np.array_equal(w.state(dtype=np.complex64), psi0)
     w.close()
