@@ -380,7 +380,10 @@ def run_gpu(args, rank, world, local):
         e2e = {"value": aggregate_throughput(2.0 * N_SITES * T_STEPS * n_e2e, te, world),
                "unit": UNIT, "h2d_bytes_per_step": int(hin.nbytes),
                "d2h_bytes_per_step": int(hP.nbytes) + 8, "steps": n_e2e,
-               "ms_per_step": [round(x, 2) for x in per_step]}
+               "ms_per_step": [round(x, 2) for x in per_step],
+               # context only: the typical step, for runs where a step or two met
+               # host-side interference (value above is the mean over all steps)
+               "value_at_median_step": 2.0 * N_SITES * T_STEPS * world / (statistics.median(per_step) / 1e3)}
 
     # the torus: the fused 2D step (k = 1) on the 8192^2 lattice, against the HBM roof
     torus = {}
