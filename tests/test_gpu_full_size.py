@@ -77,3 +77,52 @@ def test_torus_8192_streaming_sampled(qw, coin, shift):
         err = float(np.abs(got[:, y, x].astype(np.complex128) - want).max())
         assert err <= T * 4 * U32 * scale, (x, y, err, scale)
     w.close()
+
+
+def test_graph_random_regular_2e26_sampled(qw):
+    """The random 4-regular graph with 2^26 vertices (2^28 arcs), FP32, Grover, in
+    the autotuned form the benchmark times, T = 6 steps: the arcs of sampled
+    vertices against the FP64 oracle run on the ball of radius T + 1 around each
+    (arcs whose edge leaves the ball are made fixed points there; a value at the
+    centre after T steps depends only on arcs within distance T, so the cut never
+    reaches it).  Plus the norm, and the pull form bitwise against the chosen one."""
+    import torch
+    nv, T = 1 << 26, 6
+    off, partner = inputs.random_regular_arcs(nv, 4, seed=5)
+    A = int(off[-1])
+    psi0 = inputs.random_state((A,), seed=6, dtype=np.complex64)
+    w = qw.GraphWalk(off, partner, prec="f32").set_state(torch.from_numpy(psi0).cuda())
+    w.autotune()
+    w.step(T)
+    _, norm = w.probabilities()
+    assert abs(norm - 1) < T * 8 * U32
+    got = w.state(dtype=np.complex64)
+    chosen = w.variant()
+    w.set_variant(1 if chosen != 1 else 0).set_state(torch.from_numpy(psi0).cuda())
+    w.step(T)
+    assert np.array_equal(w.state(dtype=np.complex64), got)
+    w.close()
+    rng = np.random.default_rng(9)
+    for c in [0, nv - 1] + list(rng.integers(0, nv, size=4)):
+        ball, frontier = {int(c)}, [int(c)]
+        for _ in range(T + 1):
+            nxt = []
+            for v in frontier:
+                for u in (partner[4 * v: 4 * v + 4] // 4).tolist():
+                    if u not in ball:
+                        ball.add(u)
+                        nxt.append(u)
+            frontier = nxt
+        verts = np.array(sorted(ball), dtype=np.int64)
+        local = {int(v): i for i, v in enumerate(verts)}
+        arcs = (4 * verts[:, None] + np.arange(4)).ravel()
+        lpart = np.empty(len(arcs), dtype=np.int64)
+        for i, a in enumerate(arcs.tolist()):
+            p = int(partner[a])
+            lpart[i] = 4 * local[p // 4] + p % 4 if p // 4 in local else i
+        loff = np.arange(0, len(arcs) + 1, 4, dtype=np.int64)
+        want = oracle.graph_evolve(loff, lpart, psi0[arcs].astype(np.complex128), T)
+        i0 = 4 * local[int(c)]
+        err = float(np.abs(got[4 * c: 4 * c + 4].astype(np.complex128) - want[i0: i0 + 4]).max())
+        scale = float(np.sqrt((np.abs(psi0[arcs].astype(np.complex128)) ** 2).sum()))
+        assert err <= T * 8 * U32 * scale, (c, err, scale)
