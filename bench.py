@@ -360,27 +360,38 @@ def run_gpu(args, rank, world, local):
         host_in = torch.from_numpy(psi0).pin_memory()
         host_P = torch.empty(N_SITES, dtype=torch.float32).pin_memory()
         hin, hP = host_in.numpy(), host_P.numpy()
-        for _ in range(2):   # warm-up: first touches of the pinned buffers
+        time.sleep(1.0)      # let the timed region's clock sampler exit first
+        for _ in range(3):   # warm-up: first touches of the pinned buffers
             qw.qw_set_state(w.h, hin)
             qw.qw_step(w.h, T_STEPS)
             qw.qw_probabilities(w.h, hP)
         n_e2e = max(1, min(args.steps, 5))
+        # per step, CUDA events split the copy in from the steps (the rest, up to the
+        # host holding P, is the marginals and the copy out).  No clock sampler runs
+        # here: host-to-device copies measured several times slower while an
+        # nvidia-smi sampler started or stopped (the steps themselves did not)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n_e2e)]
         barrier(dist, local)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         marks = []
-        for _ in range(n_e2e):
+        for i in range(n_e2e):
+            evs[i][0].record(stream)
             qw.qw_set_state(w.h, hin)
+            evs[i][1].record(stream)
             qw.qw_step(w.h, T_STEPS)
+            evs[i][2].record(stream)
             qw.qw_probabilities(w.h, hP)   # synchronises: the host holds the step's P
             marks.append(time.perf_counter())
         torch.cuda.synchronize()
         te = max_over_ranks(dist, time.perf_counter() - t0, local)
+        phases = [[round(e[0].elapsed_time(e[1]), 2), round(e[1].elapsed_time(e[2]), 2)] for e in evs]
         per_step = [1e3 * (b - a) for a, b in zip([t0] + marks[:-1], marks)]
         e2e = {"value": aggregate_throughput(2.0 * N_SITES * T_STEPS * n_e2e, te, world),
                "unit": UNIT, "h2d_bytes_per_step": int(hin.nbytes),
                "d2h_bytes_per_step": int(hP.nbytes) + 8, "steps": n_e2e,
                "ms_per_step": [round(x, 2) for x in per_step],
+               "h2d_and_steps_ms": phases,
                # context only: the typical step, for runs where a step or two met
                # host-side interference (value above is the mean over all steps)
                "value_at_median_step": 2.0 * N_SITES * T_STEPS * world / (statistics.median(per_step) / 1e3)}
