@@ -158,6 +158,22 @@ qw_status qw_step_adjoint(qw_walk *w, int64_t T);
 qw_status qw_probabilities(qw_walk *w, void *P_out, qw_rdtype pdtype, int on_device,
                            double *norm_out);
 
+/* Run `count` independent walks of T steps from host states, the way a
+ * server would: the result is what qw_set_state(host), qw_step(T) and
+ * qw_probabilities(host) give for each input in turn, bit for bit, but the
+ * copy of state i+1 in and of the marginals of state i-1 out overlap the
+ * steps of state i (two copy streams, a third state buffer that the call
+ * allocates once).  Input i starts at amp_in + i*in_stride bytes, in the
+ * layout of qw_set_state; dtype must match the precision (QW_C64 for QW_F32,
+ * QW_C128 for QW_F64; else QW_EUNSUPPORTED).  P of run i goes to
+ * P_out + i*p_stride bytes (nsites values of pdtype), its norm to norms_out[i]
+ * (may be NULL).  A stride of 0 reuses one buffer for every run (the last
+ * run's P remains).  Host buffers should be pinned for the copies to overlap.
+ * Synchronous: returns when every P is on the host; the walk's state is then
+ * the last run's final state. */
+qw_status qw_run_host_batch(qw_walk *w, int count, const void *amp_in, int64_t in_stride, qw_cdtype dtype,
+                            int64_t T, void *P_out, int64_t p_stride, qw_rdtype pdtype, double *norms_out);
+
 /* Execution plan of qw_step: temporal depth k (steps per kernel, >= 1) and
  * tile (sites per thread in 1D, 0 = library default).  k = 0 restores the
  * default / tuned plan.  QW_EINVAL for a combination the kernels reject. */

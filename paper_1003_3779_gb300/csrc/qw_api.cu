@@ -13,6 +13,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "qw_handle.h"
 
@@ -420,6 +421,12 @@ qw_status qw_destroy(qw_walk *w) {
     cudaFree(w->p_dev);
     cudaFree(w->staging);
     cudaFree(w->grad_scratch);
+    cudaFree(w->buf3);
+    cudaFree(w->pipe_p[0]);
+    cudaFree(w->pipe_p[1]);
+    cudaFree(w->pipe_norm);
+    if (w->s_in) cudaStreamDestroy(w->s_in);
+    if (w->s_out) cudaStreamDestroy(w->s_out);
     if (w->host_scalar) cudaFreeHost(w->host_scalar);
     delete w;
     return QW_OK;
@@ -713,6 +720,120 @@ qw_status qw_probabilities(qw_walk *w, void *P_out, qw_rdtype pdtype, int on_dev
         if ((e = cudaStreamSynchronize(w->stream)) != cudaSuccess) return cuda_error(w, e, "marginals");
         if (norm_out) *norm_out = *w->host_scalar;
     }
+    return QW_OK;
+}
+
+qw_status qw_run_host_batch(qw_walk *w, int count, const void *amp_in, int64_t in_stride, qw_cdtype dtype, int64_t T,
+                            void *P_out, int64_t p_stride, qw_rdtype pdtype, double *norms_out) {
+    if (!w) return QW_EINVAL;
+    if (count < 0 || T < 0 || in_stride < 0 || p_stride < 0 || (count && (!amp_in || !P_out)) ||
+        (pdtype != QW_R64 && pdtype != QW_R32))
+        return set_error(w, QW_EINVAL, "bad count, T, strides, buffers or probability dtype");
+    if (!direct_layout(w, dtype))
+        return set_error(w, QW_EUNSUPPORTED, "pipelined runs take complex64 states for FP32 and complex128 for FP64");
+    if (count == 0) return QW_OK;
+    const size_t plane = (size_t)w->ns * (dtype == QW_C128 ? 16 : 8);
+    const size_t pb = (size_t)w->ns * (pdtype == QW_R32 ? 4 : 8);
+    cudaError_t e = cudaSuccess;
+    if (!w->buf3 && (e = dev_alloc(&w->buf3, w->state_bytes)) != cudaSuccess) return cuda_error(w, e, "third state buffer");
+    if (w->pipe_p_bytes < pb) {
+        cudaStreamSynchronize(w->stream);
+        cudaFree(w->pipe_p[0]); cudaFree(w->pipe_p[1]);
+        w->pipe_p[0] = w->pipe_p[1] = nullptr; w->pipe_p_bytes = 0;
+        if ((e = dev_alloc(&w->pipe_p[0], pb)) == cudaSuccess) e = dev_alloc(&w->pipe_p[1], pb);
+        if (e != cudaSuccess) return cuda_error(w, e, "pipelined probability buffers");
+        w->pipe_p_bytes = pb;
+    }
+    if (!w->pipe_norm && (e = dev_alloc((void **)&w->pipe_norm, 2 * sizeof(double))) != cudaSuccess)
+        return cuda_error(w, e, "pipelined norms");
+    if (!w->s_in && (e = cudaStreamCreateWithFlags(&w->s_in, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_error(w, e, "copy stream");
+    if (!w->s_out && (e = cudaStreamCreateWithFlags(&w->s_out, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_error(w, e, "copy stream");
+    // events: state i arrived; run i's buffers and P slot free again (compute done);
+    // P slot of run i copied out
+    std::vector<cudaEvent_t> ev_in(count), ev_done(count), ev_out(count);
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&ev_in[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_done[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_out[i], cudaEventDisableTiming);
+    }
+    auto destroy_events = [&]() {
+        for (int i = 0; i < count; ++i) {
+            if (ev_in[i]) cudaEventDestroy(ev_in[i]);
+            if (ev_done[i]) cudaEventDestroy(ev_done[i]);
+            if (ev_out[i]) cudaEventDestroy(ev_out[i]);
+        }
+    };
+    if (e != cudaSuccess) { destroy_events(); return cuda_error(w, e, "pipeline events"); }
+
+    // Three buffers rotate: run i reads its state from X_i and ping-pongs with
+    // Y_i; run i+1's state is copied into the third, Z_i, which run i-1 may
+    // still be using until its event, while run i computes.
+    void *bufs[3] = {w->buf[w->cur], w->buf[w->cur ^ 1], w->buf3};
+    auto copy_in = [&](int i, void *dst) -> cudaError_t {
+        cudaError_t r = cudaSuccess;
+        if (i >= 2) r = cudaStreamWaitEvent(w->s_in, ev_done[i - 2], 0);   // dst was run i-2's buffer
+        if (r == cudaSuccess)
+            r = cudaMemcpy2DAsync(dst, (size_t)w->pitch * w->slot_bytes, static_cast<const char *>(amp_in) + i * in_stride,
+                                  plane, plane, w->d, cudaMemcpyHostToDevice, w->s_in);
+        if (r == cudaSuccess) r = cudaEventRecord(ev_in[i], w->s_in);
+        return r;
+    };
+    // wait for work the caller queued on the walk's stream before touching its buffers
+    cudaEvent_t start_ev = nullptr;
+    if ((e = cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming)) == cudaSuccess &&
+        (e = cudaEventRecord(start_ev, w->stream)) == cudaSuccess &&
+        (e = cudaStreamWaitEvent(w->s_in, start_ev, 0)) == cudaSuccess)
+        e = copy_in(0, bufs[0]);
+    int x = 0;   // index in bufs of run i's input
+    qw_status st = QW_OK;
+    for (int i = 0; i < count && e == cudaSuccess && st == QW_OK; ++i) {
+        const int y = (x + 1) % 3, z = (x + 2) % 3;
+        if (i + 1 < count && (e = copy_in(i + 1, bufs[z])) != cudaSuccess) break;
+        if ((e = cudaStreamWaitEvent(w->stream, ev_in[i], 0)) != cudaSuccess) break;
+        if (i >= 2 && (e = cudaStreamWaitEvent(w->stream, ev_out[i - 2], 0)) != cudaSuccess) break;   // P slot free
+        // the walk's two buffers for this run: the arrived state and a free one
+        w->cur = 0;
+        w->buf[0] = bufs[x];
+        w->buf[1] = bufs[y];
+        w->gain_fb = 1.0;
+        w->drift_pending = 1.0;
+        if ((st = run_steps(w, T, 0)) != QW_OK) break;
+        void *pslot = w->pipe_p[i & 1];
+        e = launch_marginals(w->prec, cur_view(w), w->ns, pslot, pdtype == QW_R32, w->partials, marginal_blocks(),
+                             w->pipe_norm + (i & 1), w->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_done[i], w->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(w->s_out, ev_done[i], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(static_cast<char *>(P_out) + i * p_stride, pslot, pb, cudaMemcpyDeviceToHost, w->s_out);
+        if (e == cudaSuccess && norms_out)
+            e = cudaMemcpyAsync(norms_out + i, w->pipe_norm + (i & 1), sizeof(double), cudaMemcpyDeviceToHost, w->s_out);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_out[i], w->s_out);
+        // the run's result is in w->buf[w->cur]; the next run's input is in bufs[z]
+        const int res = w->buf[w->cur] == bufs[x] ? x : y;
+        // rotate so that the next run reads bufs[z] and ping-pongs with the
+        // buffer not holding this run's result (its P is computed already, in
+        // stream order, before the next run's first kernel)
+        const int other = res == x ? y : x;
+        void *const nz = bufs[z], *const no = bufs[other], *const nr = bufs[res];
+        bufs[0] = nz; bufs[1] = no; bufs[2] = nr;
+        x = 0;
+    }
+    // leave the walk holding the last run's result as its state
+    cudaError_t e2 = cudaStreamSynchronize(w->s_in);
+    cudaError_t e3 = cudaStreamSynchronize(w->s_out);
+    cudaError_t e4 = cudaStreamSynchronize(w->stream);
+    // after the loop bufs[2] holds the last result; the other two are free
+    w->buf[0] = bufs[2];
+    w->buf[1] = bufs[1];
+    w->buf3 = bufs[0];
+    w->cur = 0;
+    if (start_ev) cudaEventDestroy(start_ev);
+    destroy_events();
+    if (st != QW_OK) return st;
+    if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : e4);
+    if (e != cudaSuccess) return cuda_error(w, e, "pipelined runs");
     return QW_OK;
 }
 

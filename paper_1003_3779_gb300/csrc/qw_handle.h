@@ -53,6 +53,13 @@ struct qw_walk {
     // staging for host conversions
     void *staging = nullptr;
     size_t staging_bytes = 0;
+    // pipelined host runs (qw_run_host_batch): a third state buffer, two
+    // probability / norm slots and the copy streams
+    void *buf3 = nullptr;
+    void *pipe_p[2] = {nullptr, nullptr};
+    size_t pipe_p_bytes = 0;
+    double *pipe_norm = nullptr;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
 
     // execution plan
     int plan_k = 0, plan_tile = 0;

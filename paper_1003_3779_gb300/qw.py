@@ -55,6 +55,7 @@ def lib():
         "qw_set_coin_phases": (I, [P, P, P, I]),
         "qw_set_links": (I, [P, P, I]),
         "qw_set_link_noise": (I, [P, ctypes.c_double, ctypes.c_uint64, I64]),
+        "qw_run_host_batch": (I, [P, I, P, I64, I, I64, P, I64, I, P]),
         "qw_get_link_step": (I, [P, P]),
         "qw_set_state": (I, [P, P, I, I]),
         "qw_get_state": (I, [P, P, I, I]),
@@ -346,6 +347,26 @@ class Walk:
     def set_links(self, closed):
         qw_set_links(self.h, closed)
         return self
+
+    def run_host_batch(self, states, T, count=None, P_out=None, norms=False):
+        """Independent runs of T steps from host states, copies overlapping the
+        steps (qw_run_host_batch).  states: (count, d, ...) numpy array, or one
+        state (d, ...) reused `count` times.  P_out: (count, ...) or one plane
+        shape (reused, the last run's P remains); float32 or float64, allocated
+        if None.  Returns P_out (and the norms if `norms`)."""
+        states = np.ascontiguousarray(states)
+        if count is None:
+            count, in_stride = states.shape[0], states[0].nbytes
+        else:
+            in_stride = 0
+        if P_out is None:
+            P_out = np.empty((count,) + self.plane_shape, dtype=np.float64)
+        p_stride = P_out[0].nbytes if P_out.shape != self.plane_shape else 0
+        nrm = np.empty(max(count, 1), dtype=np.float64) if norms else None
+        _check(lib().qw_run_host_batch(self.h, int(count), _ptr(states), int(in_stride), _cdtype(states), int(T),
+                                       _ptr(P_out), int(p_stride), R32 if P_out.dtype == np.float32 else R64,
+                                       _ptr(nrm)), self.h)
+        return (P_out, nrm[:count]) if norms else P_out
 
     def set_link_noise(self, p, seed, step=0):
         """Links broken at random afresh at every step with probability p."""
