@@ -149,8 +149,9 @@ __device__ __forceinline__ void load_vertex(const Cx<R> *__restrict__ in, int v,
 template <class R, int MODE, int DR>
 __global__ void __launch_bounds__(GR_THREADS)
 k_graph_push(GraphArgs<R> g, const Cx<R> *__restrict__ in, Cx<R> *__restrict__ out) {
-    const int a = blockIdx.x * GR_THREADS + threadIdx.x;
-    if (a >= g.A) return;
+    const long long a64 = (long long)blockIdx.x * GR_THREADS + threadIdx.x;   // A < 2^31: 64-bit before the check
+    if (a64 >= g.A) return;
+    const int a = (int)a64;
     int v, o, d;
     vertex_of<DR>(g, a, v, o, d);
     out[__ldg(g.partner + a)] = coin_row<MODE, DR, 0>(g, in, v, o, d, a - o);
@@ -160,8 +161,9 @@ k_graph_push(GraphArgs<R> g, const Cx<R> *__restrict__ in, Cx<R> *__restrict__ o
 template <class R, int MODE, int DR>
 __global__ void __launch_bounds__(GR_THREADS)
 k_graph_pull(GraphArgs<R> g, const Cx<R> *__restrict__ in, Cx<R> *__restrict__ out) {
-    const int a = blockIdx.x * GR_THREADS + threadIdx.x;
-    if (a >= g.A) return;
+    const long long a64 = (long long)blockIdx.x * GR_THREADS + threadIdx.x;
+    if (a64 >= g.A) return;
+    const int a = (int)a64;
     const int b = __ldg(g.partner + a);
     int v, o, d;
     vertex_of<DR>(g, b, v, o, d);
@@ -172,8 +174,9 @@ k_graph_pull(GraphArgs<R> g, const Cx<R> *__restrict__ in, Cx<R> *__restrict__ o
 template <class R, int MODE, int DR>
 __global__ void __launch_bounds__(GR_THREADS)
 k_graph_adjoint(GraphArgs<R> g, const Cx<R> *__restrict__ in, Cx<R> *__restrict__ out) {
-    const int a = blockIdx.x * GR_THREADS + threadIdx.x;
-    if (a >= g.A) return;
+    const long long a64 = (long long)blockIdx.x * GR_THREADS + threadIdx.x;
+    if (a64 >= g.A) return;
+    const int a = (int)a64;
     int v, o, d;
     vertex_of<DR>(g, a, v, o, d);
     out[a] = coin_row<MODE, DR, 1>(g, in, v, o, d, a - o);
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(GR_THREADS)
 k_graph_bucket(GraphArgs<R> g, const Cx<R> *__restrict__ in, const unsigned short *__restrict__ lpos,
                const int *__restrict__ gsl, Cx<R> *__restrict__ tmp) {
     __shared__ Cx<R> sm[GR_TILE];
-    const int base = blockIdx.x * GR_TILE;
+    const int base = blockIdx.x * GR_TILE;   // < A: the grid has ceil(A / GR_TILE) blocks
     const int n = min(GR_TILE, g.A - base);
     if constexpr (DR > 0) {
         // a thread per vertex: one vector load of its DR amplitudes (GR_TILE is
@@ -215,7 +218,7 @@ k_graph_bucket(GraphArgs<R> g, const Cx<R> *__restrict__ in, const unsigned shor
 template <class R>
 __global__ void __launch_bounds__(GR_THREADS)
 k_graph_scatter(int A, const int *__restrict__ dst, const Cx<R> *__restrict__ tmp, Cx<R> *__restrict__ out) {
-    const int s = blockIdx.x * GR_THREADS + threadIdx.x;
+    const long long s = (long long)blockIdx.x * GR_THREADS + threadIdx.x;
     if (s < A) out[__ldg(dst + s)] = tmp[s];
 }
 
@@ -240,14 +243,14 @@ __device__ __forceinline__ Cx<double> ldcg(const Cx<double> *p) {
 template <class R>
 __global__ void __launch_bounds__(GR_THREADS)
 k_graph_gather(int A, const int *__restrict__ srcs, const Cx<R> *__restrict__ tmp, Cx<R> *__restrict__ out, int pf) {
-    const int a0 = blockIdx.x * (GR_THREADS * GR_GATHER) + threadIdx.x;
+    const long long a0 = (long long)blockIdx.x * (GR_THREADS * GR_GATHER) + threadIdx.x;
     int sl[GR_GATHER];
     Cx<R> v[GR_GATHER];
 #pragma unroll
     for (int k = 0; k < GR_GATHER; ++k) {
-        const int a = a0 + k * GR_THREADS;
+        const long long a = a0 + k * GR_THREADS;
         if (a < A) {
-            if (pf > 0 && a < A - pf) asm volatile("prefetch.global.L2 [%0];" ::"l"(tmp + a + pf));
+            if (pf > 0 && a < (long long)A - pf) asm volatile("prefetch.global.L2 [%0];" ::"l"(tmp + a + pf));
             sl[k] = __ldcs(srcs + a);
         }
     }
@@ -256,7 +259,7 @@ k_graph_gather(int A, const int *__restrict__ srcs, const Cx<R> *__restrict__ tm
         if (a0 + k * GR_THREADS < A) v[k] = ldcg(tmp + sl[k]);
 #pragma unroll
     for (int k = 0; k < GR_GATHER; ++k) {
-        const int a = a0 + k * GR_THREADS;
+        const long long a = a0 + k * GR_THREADS;
         if (a >= A) continue;
         if constexpr (sizeof(R) == 4) {
             __stcs(reinterpret_cast<float2 *>(out + a), make_float2(v[k].re, v[k].im));
@@ -303,7 +306,7 @@ __global__ void __launch_bounds__(GR_THREADS)
 k_graph_marginals(const int *__restrict__ off, int nvert, const Cx<R> *__restrict__ psi, PO *P, double *partials) {
     __shared__ double sh[GR_THREADS / 32];
     double acc = 0.0;
-    for (int v = blockIdx.x * GR_THREADS + threadIdx.x; v < nvert; v += gridDim.x * GR_THREADS) {
+    for (long long v = (long long)blockIdx.x * GR_THREADS + threadIdx.x; v < nvert; v += (long long)gridDim.x * GR_THREADS) {
         R p = R(0);
         for (int a = off[v]; a < off[v + 1]; ++a) p += psi[a].re * psi[a].re + psi[a].im * psi[a].im;
         if (P) P[v] = (PO)p;
@@ -413,7 +416,7 @@ GraphArgs<R> args_of(const qw_gwalk *g) {
 // kernel: 0 push, 1 pull, 2 adjoint
 template <class R, int MODE, int DR>
 cudaError_t launch_mode_dr(const GraphArgs<R> &a, int kernel, const Cx<R> *in, Cx<R> *out, cudaStream_t s) {
-    const unsigned blocks = (unsigned)((a.A + GR_THREADS - 1) / GR_THREADS);
+    const unsigned blocks = (unsigned)(((long long)a.A + GR_THREADS - 1) / GR_THREADS);
     if (kernel == 0) k_graph_push<R, MODE, DR><<<blocks, GR_THREADS, 0, s>>>(a, in, out);
     else if (kernel == 1) k_graph_pull<R, MODE, DR><<<blocks, GR_THREADS, 0, s>>>(a, in, out);
     else k_graph_adjoint<R, MODE, DR><<<blocks, GR_THREADS, 0, s>>>(a, in, out);
@@ -422,7 +425,7 @@ cudaError_t launch_mode_dr(const GraphArgs<R> &a, int kernel, const Cx<R> *in, C
 
 template <class R, int MODE, int DR>
 cudaError_t launch_bucket_dr(const GraphArgs<R> &a, const qw_gwalk *g, const Cx<R> *in) {
-    const unsigned tiles = (unsigned)((a.A + GR_TILE - 1) / GR_TILE);
+    const unsigned tiles = (unsigned)(((long long)a.A + GR_TILE - 1) / GR_TILE);
     k_graph_bucket<R, MODE, DR><<<tiles, GR_THREADS, 0, g->stream>>>(a, in, g->lpos_dev, g->gsl_dev,
                                                                        static_cast<Cx<R> *>(g->tmp_dev));
     return cudaGetLastError();
@@ -465,11 +468,11 @@ cudaError_t graph_step(qw_gwalk *g, int kernel) {
             default: e = launch_bucket<R, QW_GCOIN_PER_VERTEX>(g, a, in); break;
         }
         if (e != cudaSuccess) return e;
-        const unsigned blocks = (unsigned)((a.A + GR_THREADS - 1) / GR_THREADS);
+        const unsigned blocks = (unsigned)(((long long)a.A + GR_THREADS - 1) / GR_THREADS);
         const Cx<R> *tmp = static_cast<const Cx<R> *>(g->tmp_dev);
         if (kernel == 3) k_graph_scatter<R><<<blocks, GR_THREADS, 0, g->stream>>>(a.A, g->dst_dev, tmp, out);
         else
-            k_graph_gather<R><<<(unsigned)((a.A + GR_THREADS * GR_GATHER - 1) / (GR_THREADS * GR_GATHER)), GR_THREADS, 0,
+            k_graph_gather<R><<<(unsigned)(((long long)a.A + GR_THREADS * GR_GATHER - 1) / (GR_THREADS * GR_GATHER)), GR_THREADS, 0,
                                 g->stream>>>(a.A, g->slot_dev, tmp, out, g->window_arcs);
         return cudaGetLastError();
     }
@@ -505,14 +508,14 @@ qw_status ensure_two_pass(qw_gwalk *g) {
     std::vector<unsigned short> lpos((size_t)A);
     std::vector<int> gsl((size_t)A), dst((size_t)A), slot((size_t)A);
     std::vector<int> lcnt((size_t)nb), lstart((size_t)nb);
-    for (int base = 0; base < A; base += GR_TILE) {
-        const int n = std::min(GR_TILE, A - base);
+    for (int64_t base = 0; base < A; base += GR_TILE) {
+        const int n = (int)std::min<int64_t>(GR_TILE, A - base);
         std::fill(lcnt.begin(), lcnt.end(), 0);
         for (int i = 0; i < n; ++i) ++lcnt[(size_t)(partner[(size_t)(base + i)] / W)];
         int acc = 0;
         for (int b = 0; b < nb; ++b) { lstart[(size_t)b] = acc; acc += lcnt[(size_t)b]; }
         for (int i = 0; i < n; ++i) {
-            const int a = base + i;
+            const int a = (int)(base + i);
             const int b = (int)(partner[(size_t)a] / W);
             const int place = lstart[(size_t)b]++;
             const int s = (int)ptr[(size_t)b]++;
