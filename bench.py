@@ -437,7 +437,34 @@ def run_gpu(args, rank, world, local):
                                           ("hbm_gbs" if kk == 1 else "effective_gbs"): gbs,
                                           "frac_of_measured": gbs / hbm_gbs, "frac_of_8000": gbs / 8000.0}
             w2.close()
-        del z
+        # the rows beyond the periodic lattice walk, same lattice and state: the
+        # diagonal lattice (fused step), and the generic kernel with a segment
+        # boundary and 5 % of the links closed (fixed mask, 2 more bytes per
+        # site-step), or with links closed at random afresh at every step
+        # (p = 0.05, Philox in the kernel, no mask traffic)
+        mask = (torch.rand((2, L * L), generator=torch.Generator().manual_seed(3)) < 0.05).to(torch.uint8).cuda()
+        for name, kw, setup, nbytes in (
+                ("diagonal_hh", dict(shift=qw.SHIFT_DIAGONAL), lambda w_: w_.set_coin(_in.hadamard2()), 64.0),
+                ("segment_fixed_links_5pct", dict(bc=qw.BC_SEGMENT),
+                 lambda w_: w_.set_coin(_in.grover()).set_links(mask), 66.0),
+                ("random_links_5pct_per_step", dict(),
+                 lambda w_: w_.set_coin(_in.grover()).set_link_noise(0.05, 11), 64.0)):
+            w2 = qw.Walk((L, L), prec="f32", **kw)
+            setup(w2)
+            w2.set_state(z)
+            w2.step(8)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            w2.step(64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts = a.elapsed_time(b) / 1e3 / 64
+            gbs = nbytes * L * L / ts / 1e9
+            torus[name] = {"site_coin_updates_per_s": 4.0 * L * L / ts, "ms_per_step": ts * 1e3,
+                           "kernel": w2.describe()["path"], "algorithmic_bytes_per_site_step": nbytes,
+                           "hbm_gbs": gbs, "frac_of_measured": gbs / hbm_gbs, "norm": w2.norm()}
+            w2.close()
+        del z, mask
 
     # batched walks: 4096 walks in one persistent launch (graph replay), FP32 and bf16 storage
     batch = {}
@@ -588,6 +615,24 @@ def run_case(args):
         gw.close()
         print(json.dumps(out))
         return
+    if args.case == "generic":
+        # the generic kernel on an L x L torus (--n-sites L, default 4096), Grover,
+        # links closed at random afresh at every step (p = 0.05)
+        L = args.n_sites if args.n_sites != N_SITES else 4096
+        g = torch.Generator(device="cuda").manual_seed(2)
+        z = torch.randn((4, L, L), dtype=torch.complex64, device="cuda", generator=g)
+        z /= z.abs().pow(2).sum().sqrt()
+        w = qw.Walk((L, L), prec="f32").set_coin(_in.grover()).set_link_noise(0.05, 11).set_state(z)
+        w.step(2)
+        a, b = ev(), ev()
+        a.record(stream)
+        w.step(args.steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out.update(L=L, path=w.describe()["path"], ms_per_step=a.elapsed_time(b) / args.steps)
+        w.close()
+        print(json.dumps(out))
+        return
     if args.case == "torus":
         L = args.n_sites
         g = torch.Generator(device="cuda").manual_seed(2)
@@ -642,7 +687,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--n-sites", type=int, default=N_SITES,
                     help="cycle length (default 2^27; smaller only for profiling captures)")
-    ap.add_argument("--case", default="", choices=["", "torus", "batch", "grad", "graph"],
+    ap.add_argument("--case", default="", choices=["", "torus", "batch", "grad", "graph", "generic"],
                     help="run a small named workload for kernel captures instead of the benchmark")
     ap.add_argument("--walks", type=int, default=4096, help="walks of the batch case")
     ap.add_argument("--plan", default="",

@@ -121,10 +121,10 @@ qw_status qw_set_links(qw_walk *w, const uint8_t *closed, int on_device);
 
 /* Links broken at random afresh at every step (Sec. 3, RBL resampled per
  * step), on top of the fixed mask of qw_set_links.  The link of axis a
- * (0: x, 1: y) at link site v = y*nx + x is closed during step t when word 0
- * of Philox4x32-10 (Salmon et al., SC 2011) with counter
- * (v mod 2^32, v >> 32, t mod 2^32, a) and key (seed mod 2^32, seed >> 32)
- * is below floor(p * 2^32) (capped at 2^32 - 1).  p in [0, 1]; p = 0 turns it
+ * (0: x, 1: y) at link site v = y*nx + x (the link from v to its +a
+ * neighbour) is closed during step t when word a of Philox4x32-10 (Salmon et
+ * al., SC 2011) with counter (v mod 2^32, v >> 32, t mod 2^32, 0) and key
+ * (seed mod 2^32, seed >> 32) is below floor(p * 2^32) (capped at 2^32 - 1).  p in [0, 1]; p = 0 turns it
  * off.  `step` is the index t of the next forward step: qw_step uses t and
  * counts up, qw_step_adjoint counts down and then uses t, so a forward run
  * followed by its adjoint retraces the same masks.  QW_EINVAL for p outside

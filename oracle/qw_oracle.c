@@ -354,8 +354,9 @@ int oracle_region_grad(const int64_t *dims, int shift, const double *base,
  * M1 = 0xCD9E8D57, and the key grows by (0x9E3779B9, 0xBB67AE85) before every
  * round after the first.
  *
- * Link (axis, site) is closed at step t when word 0 of Philox(counter =
- * (site low 32 bits, site high 32 bits, t, axis), key = (seed low, seed high))
+ * The two links a site owns (to its +x and +y neighbours) share one draw:
+ * link (axis, site) is closed at step t when word `axis` of Philox(counter =
+ * (site low 32 bits, site high 32 bits, t, 0), key = (seed low, seed high))
  * is below the threshold (the closing probability times 2^32).
  */
 void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
@@ -383,13 +384,13 @@ int oracle_link_masks(int ndim, const int64_t *dims, uint64_t seed, uint32_t thr
     int64_t ns = dims[0] * (ndim == 2 ? dims[1] : 1);
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     for (int64_t t = 0; t < T; ++t)
-        for (int axis = 0; axis < ndim; ++axis)
-            for (int64_t v = 0; v < ns; ++v) {
-                uint32_t ctr[4] = {(uint32_t)v, (uint32_t)((uint64_t)v >> 32), (uint32_t)(t0 + t), (uint32_t)axis};
-                uint32_t r[4];
-                oracle_philox4x32_10(ctr, key, r);
-                out[((size_t)t * ndim + axis) * ns + v] = r[0] < threshold;
-            }
+        for (int64_t v = 0; v < ns; ++v) {
+            uint32_t ctr[4] = {(uint32_t)v, (uint32_t)((uint64_t)v >> 32), (uint32_t)(t0 + t), 0};
+            uint32_t r[4];
+            oracle_philox4x32_10(ctr, key, r);
+            for (int axis = 0; axis < ndim; ++axis)
+                out[((size_t)t * ndim + axis) * ns + v] = r[axis] < threshold;
+        }
     return OR_OK;
 }
 

@@ -22,12 +22,12 @@ struct GenGeom {
     uint32_t rthr, rk0, rk1, rstep;   // links broken at random at this step (rthr 0: none)
 };
 
-// Word 0 of Philox4x32 with 10 rounds (Salmon, Moraes, Dror and Shaw, SC 2011)
-// for counter (c0, c1, c2, c3) and key (k0, k1): each round multiplies c0 and
-// c2 by 0xD2511F53 and 0xCD9E8D57 and mixes the product halves with c1, c3 and
-// the key, which then grows by (0x9E3779B9, 0xBB67AE85).
-__device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                                 uint32_t k0, uint32_t k1) {
+// Words 0 and 1 of Philox4x32 with 10 rounds (Salmon, Moraes, Dror and Shaw, SC
+// 2011) for counter (c0, c1, c2, c3) and key (k0, k1): each round multiplies c0
+// and c2 by 0xD2511F53 and 0xCD9E8D57 and mixes the product halves with c1, c3
+// and the key, which then grows by (0x9E3779B9, 0xBB67AE85).
+__device__ __forceinline__ uint2 philox_words01(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                                uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         const uint32_t h0 = __umulhi(0xD2511F53u, c0), l0 = 0xD2511F53u * c0;
@@ -37,7 +37,15 @@ __device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint3
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
-    return c0;
+    return make_uint2(c0, c1);
+}
+
+// Is the link from (lx, ly) to its +axis neighbour broken at random at this
+// step?  The site's two links share one draw: word `axis` below the threshold.
+__device__ __forceinline__ bool random_closed(const GenGeom &g, int axis, int64_t lx, int64_t ly) {
+    const uint64_t v = (uint64_t)(ly * g.nx + lx);
+    const uint2 w = philox_words01((uint32_t)v, (uint32_t)(v >> 32), g.rstep, 0u, g.rk0, g.rk1);
+    return (axis == 0 ? w.x : w.y) < g.rthr;
 }
 
 // Axis and sign of coin c: 1D coin 0 -> -x, coin 1 -> +x; 2D 0 +x, 1 -x, 2 +y, 3 -y.
@@ -59,10 +67,7 @@ __device__ __forceinline__ int move_along(const GenGeom &g, int64_t x, int64_t y
     bool closed = false;
     const int64_t lx = axis == 0 ? lp : x, ly = axis == 0 ? y : lp;
     if (g.links) closed = g.links[axis * g.ns + ly * g.nx + lx] != 0;
-    if (!closed && g.rthr) {   // broken at random at this step (Sec. 3, the RBL function)
-        const uint64_t v = (uint64_t)(ly * g.nx + lx);
-        closed = philox_word0((uint32_t)v, (uint32_t)(v >> 32), g.rstep, (uint32_t)axis, g.rk0, g.rk1) < g.rthr;
-    }
+    if (!closed && g.rthr) closed = random_closed(g, axis, lx, ly);   // broken at random (Sec. 3, RBL)
     if (edge && g.bc == QW_BC_SEGMENT) closed = true;
     int64_t q = p + sgn;
     q = q < 0 ? n - 1 : (q == n ? 0 : q);
@@ -178,6 +183,94 @@ k_step_generic(View in, View out, GenGeom g, int adjoint, CoinP<typename St<P>::
             C acc = czero<real>();
             for (int r = 0; r < d; ++r) acc = cadd(acc, conjmul(gen_entry<CK, real>(cp, coins, e, d, v, r, k), b[r]));
             S::st(out, k, v, rmul(gain, acc));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The common generic case in 2D tiles: forward step, moving or flip-flop shift,
+// one global coin, any boundary, fixed and/or random link masks.  A block owns
+// GT_X x gt_y<P>() sites.  It computes phi = C psi once for them and a one-site
+// halo into shared memory, and the state of every link the tile needs once (a
+// site's +x and +y links from one Philox draw), then each site pulls its four
+// incoming amplitudes from shared memory.  Per output the arithmetic is that of
+// k_step_generic (same coin row, same order), so the two agree bit for bit;
+// k_step_generic evaluates the coin row and the link again for every output.
+constexpr int GT_X = 64, GT_THREADS = 256;
+template <int P>
+constexpr int gt_y() { return sizeof(Cx<typename St<P>::real>) > 8 ? 8 : 16; }
+
+// state of the link from (lx, ly) to its +axis neighbour: 0 open, 1 closed
+// (reflect), 2 absorbed (line boundary); `rnd` is the site's random draw
+__device__ __forceinline__ unsigned char link_state(const GenGeom &g, int axis, int lx, int ly, uint32_t rnd) {
+    bool closed = false;
+    if (g.links) closed = g.links[axis * g.ns + (int64_t)ly * g.nx + lx] != 0;
+    if (g.rthr && rnd < g.rthr) closed = true;
+    const bool edge = axis == 0 ? lx == g.nx - 1 : ly == g.ny - 1;
+    if (edge && g.bc == QW_BC_SEGMENT) closed = true;
+    if (closed) return 1;
+    return (edge && g.bc == QW_BC_LINE) ? 2 : 0;
+}
+
+template <int P, int SHIFT>
+__global__ void __launch_bounds__(GT_THREADS)
+k_step_generic_tile(View in, View out, GenGeom g, CoinP<typename St<P>::real> cp, typename St<P>::real gain) {
+    using real = typename St<P>::real;
+    using S = St<P>;
+    using C = Cx<real>;
+    constexpr int GY = gt_y<P>();
+    constexpr int EX = GT_X + 2, EY = GY + 2;
+    __shared__ C ph[4][EY][EX];                        // phi of the tile and its halo
+    __shared__ unsigned char ls[2][GY + 1][GT_X + 1];  // link states, owners from (x0 - 1, y0 - 1)
+    const int nx = (int)g.nx, ny = (int)g.ny;          // both < 2^31 (launcher)
+    const int x0 = blockIdx.x * GT_X, y0 = blockIdx.y * GY;
+    for (int i = threadIdx.x; i < EX * EY; i += GT_THREADS) {
+        const int ex = i % EX, ey = i / EX;
+        int gx = x0 - 1 + ex, gy = y0 - 1 + ey;       // in [-1, n + GT_X]: wrap
+        gx = gx < 0 ? gx + nx : (gx >= nx ? gx % nx : gx);
+        gy = gy < 0 ? gy + ny : (gy >= ny ? gy % ny : gy);
+        const int64_t u = (int64_t)gy * nx + gx;
+        C a[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] = S::ld(in, k, u);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            C val = czero<real>();
+#pragma unroll
+            for (int k = 0; k < 4; ++k) val = cfma(C{cp.re[r * 4 + k], cp.im[r * 4 + k]}, a[k], val);
+            ph[r][ey][ex] = val;
+        }
+        if (ex <= GT_X && ey <= GY) {
+            uint2 rnd = make_uint2(0u, 0u);
+            if (g.rthr) rnd = philox_words01((uint32_t)u, (uint32_t)((uint64_t)u >> 32), g.rstep, 0u, g.rk0, g.rk1);
+            ls[0][ey][ex] = link_state(g, 0, gx, gy, rnd.x);
+            ls[1][ey][ex] = link_state(g, 1, gx, gy, rnd.y);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < GT_X * GY; i += GT_THREADS) {
+        const int tx = i % GT_X, ty = i / GT_X;
+        const int x = x0 + tx, y = y0 + ty;
+        if (x >= nx || y >= ny) continue;
+        const int ex = tx + 1, ey = ty + 1;
+        const int64_t v = (int64_t)y * nx + x;
+#pragma unroll
+        for (int co = 0; co < 4; ++co) {
+            // the neighbour that feeds (v, co) and the link to it, as in move_along
+            int nbx, nby, st;
+            if (SHIFT == QW_SHIFT_MOVING) {   // from v - e_co, same coin
+                nbx = ex + (co == 0 ? -1 : (co == 1 ? 1 : 0));
+                nby = ey + (co == 2 ? -1 : (co == 3 ? 1 : 0));
+                st = co == 0 ? ls[0][ey][ex - 1] : (co == 1 ? ls[0][ey][ex] : (co == 2 ? ls[1][ey - 1][ex] : ls[1][ey][ex]));
+            } else {                          // from v + e_co, coin co ^ 1
+                nbx = ex + (co == 0 ? 1 : (co == 1 ? -1 : 0));
+                nby = ey + (co == 2 ? 1 : (co == 3 ? -1 : 0));
+                st = co == 0 ? ls[0][ey][ex] : (co == 1 ? ls[0][ey][ex - 1] : (co == 2 ? ls[1][ey][ex] : ls[1][ey - 1][ex]));
+            }
+            C val = czero<real>();
+            if (st == 0) val = ph[SHIFT == QW_SHIFT_MOVING ? co : (co ^ 1)][nby][nbx];
+            else if (st == 1) val = ph[SHIFT == QW_SHIFT_MOVING ? (co ^ 1) : co][ey][ex];
+            S::st(out, co, v, rmul(gain, val));
         }
     }
 }

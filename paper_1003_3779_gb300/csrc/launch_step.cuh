@@ -256,9 +256,29 @@ static void gogen(const StepGenericArgs &a, const CoinP<typename St<P>::real> &c
         real_from_double<typename St<P>::real>(a.gain));
 }
 
+// The tiled form serves the forward 2D step with one global coin on the axis
+// lattice (any boundary, fixed and random links); the grid's y extent limits
+// ny to 65535 tiles.
+template <int P>
+static bool generic_tile_ok(const StepGenericArgs &a) {
+    return a.ndim == 2 && !a.adjoint && (a.shift == QW_SHIFT_MOVING || a.shift == QW_SHIFT_FLIPFLOP) &&
+           a.kind != CK_PERSITE && a.kind != CK_PHASE && a.nx < (int64_t(1) << 30) &&
+           (a.ny + gt_y<P>() - 1) / gt_y<P>() <= 65535;
+}
+
 template <int P>
 cudaError_t generic_t(const StepGenericArgs &a, const void *coinp, cudaStream_t s) {
     const auto &cp = *static_cast<const CoinP<typename St<P>::real> *>(coinp);
+    if (generic_tile_ok<P>(a)) {
+        GenGeom g{a.ndim, a.nx, a.ny, a.nx * a.ny, a.shift, a.bc, a.links, a.rthr, a.rk0, a.rk1, a.rstep};
+        const dim3 grid((unsigned)((a.nx + GT_X - 1) / GT_X), (unsigned)((a.ny + gt_y<P>() - 1) / gt_y<P>()));
+        const auto gain = real_from_double<typename St<P>::real>(a.gain);
+        if (a.shift == QW_SHIFT_MOVING)
+            k_step_generic_tile<P, QW_SHIFT_MOVING><<<grid, GT_THREADS, 0, s>>>(a.in, a.out, g, cp, gain);
+        else
+            k_step_generic_tile<P, QW_SHIFT_FLIPFLOP><<<grid, GT_THREADS, 0, s>>>(a.in, a.out, g, cp, gain);
+        return cudaGetLastError();
+    }
     switch (a.kind) {
         case CK_PERSITE: gogen<P, CK_PERSITE>(a, cp, s); break;
         case CK_PHASE: gogen<P, CK_PHASE>(a, cp, s); break;

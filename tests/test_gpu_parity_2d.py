@@ -210,3 +210,30 @@ def test_diagonal_hadamard_factorises_on_gpu(qw):
     neg = (-np.arange(L)) % L
     assert np.abs(P - np.outer(Py[neg], Px[neg])).max() < 1e-13
     w.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("bc", [0, 1, 2])
+@pytest.mark.parametrize("shift", [0, 1])
+@pytest.mark.parametrize("dims", [(200, 37), (129, 70), (3, 5)])
+def test_tiled_generic_step_multi_tile(qw, prec, bc, shift, dims):
+    """The tiled generic step (64 x 16 or 64 x 8 sites per block, one-site halo
+    in shared memory): several tiles with ragged edges, wrap-around, a fixed
+    mask and links broken at random per step, against the oracle; the adjoint
+    (the per-site kernel) undoes it."""
+    Lx, Ly = dims
+    rng = np.random.default_rng(Lx + 7 * bc + 3 * shift)
+    C = inputs.random_unitary(4, rng)
+    fixed = (rng.uniform(size=(2, Lx * Ly)) < 0.1).astype(np.uint8)
+    psi0 = inputs.random_state((4, Ly, Lx), seed=28)
+    T, seed, p = 11, 99, 0.2
+    masks = oracle.link_masks((Ly, Lx), seed, p, 0, T) | fixed[None]
+    want = oracle.evolve(psi0, C, T, shift=shift, bc=bc, closed=masks, closed_per_step=True)
+    w = qw.Walk((Lx, Ly), prec=prec, shift=shift, bc=bc).set_coin(C).set_links(fixed).set_link_noise(p, seed)
+    w.set_state(psi0)
+    w.step(T)
+    assert maxabs(w.state(), want) < amp_tol(prec, T)
+    if bc != 2 and prec in ("f64", "comp"):
+        w.step_adjoint(T)
+        assert maxabs(w.state(), psi0) < 2 * amp_tol(prec, T)
+    w.close()
