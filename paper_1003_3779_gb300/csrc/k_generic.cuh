@@ -275,4 +275,61 @@ k_step_generic_tile(View in, View out, GenGeom g, CoinP<typename St<P>::real> cp
     }
 }
 
+// The same on the cycle: a block owns GT1_X sites, phi of them and a one-site
+// halo in shared memory, the state of links x0 - 1 .. x0 + GT1_X - 1 once.
+// 1D coins: 0 moves to x - 1, 1 to x + 1; a site's link (to x + 1) is word 0 of
+// its draw.
+constexpr int GT1_X = 1024;
+
+template <int P, int SHIFT>
+__global__ void __launch_bounds__(GT_THREADS)
+k_step_generic_tile1d(View in, View out, GenGeom g, CoinP<typename St<P>::real> cp, typename St<P>::real gain) {
+    using real = typename St<P>::real;
+    using S = St<P>;
+    using C = Cx<real>;
+    constexpr int EX = GT1_X + 2;
+    __shared__ C ph[2][EX];
+    __shared__ unsigned char ls[GT1_X + 1];      // links owned by x0 - 1 .. x0 + GT1_X - 1
+    const int nx = (int)g.nx;                    // < 2^31 (launcher)
+    const int x0 = blockIdx.x * GT1_X;
+    for (int ex = threadIdx.x; ex < EX; ex += GT_THREADS) {
+        int gx = x0 - 1 + ex;
+        gx = gx < 0 ? gx + nx : (gx >= nx ? gx % nx : gx);
+        const C a0 = S::ld(in, 0, gx), a1 = S::ld(in, 1, gx);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            C val = czero<real>();
+            val = cfma(C{cp.re[r * 2], cp.im[r * 2]}, a0, val);
+            val = cfma(C{cp.re[r * 2 + 1], cp.im[r * 2 + 1]}, a1, val);
+            ph[r][ex] = val;
+        }
+        if (ex <= GT1_X) {
+            uint32_t rnd = 0u;
+            if (g.rthr) rnd = philox_words01((uint32_t)gx, 0u, g.rstep, 0u, g.rk0, g.rk1).x;
+            ls[ex] = link_state(g, 0, gx, 0, rnd);
+        }
+    }
+    __syncthreads();
+    for (int tx = threadIdx.x; tx < GT1_X; tx += GT_THREADS) {
+        const int x = x0 + tx;
+        if (x >= nx) break;
+        const int ex = tx + 1;
+#pragma unroll
+        for (int co = 0; co < 2; ++co) {
+            int nb, st;
+            if (SHIFT == QW_SHIFT_MOVING) {   // from x + 1 (coin 0) or x - 1 (coin 1), same coin
+                nb = co == 0 ? ex + 1 : ex - 1;
+                st = co == 0 ? ls[ex] : ls[ex - 1];
+            } else {                          // from x - 1 (coin 0) or x + 1 (coin 1), coin co ^ 1
+                nb = co == 0 ? ex - 1 : ex + 1;
+                st = co == 0 ? ls[ex - 1] : ls[ex];
+            }
+            C val = czero<real>();
+            if (st == 0) val = ph[SHIFT == QW_SHIFT_MOVING ? co : (co ^ 1)][nb];
+            else if (st == 1) val = ph[SHIFT == QW_SHIFT_MOVING ? (co ^ 1) : co][ex];
+            S::st(out, co, x, rmul(gain, val));
+        }
+    }
+}
+
 }  // namespace qw

@@ -261,14 +261,25 @@ static void gogen(const StepGenericArgs &a, const CoinP<typename St<P>::real> &c
 // ny to 65535 tiles.
 template <int P>
 static bool generic_tile_ok(const StepGenericArgs &a) {
-    return a.ndim == 2 && !a.adjoint && (a.shift == QW_SHIFT_MOVING || a.shift == QW_SHIFT_FLIPFLOP) &&
-           a.kind != CK_PERSITE && a.kind != CK_PHASE && a.nx < (int64_t(1) << 30) &&
-           (a.ny + gt_y<P>() - 1) / gt_y<P>() <= 65535;
+    if (a.adjoint || !(a.shift == QW_SHIFT_MOVING || a.shift == QW_SHIFT_FLIPFLOP) || a.kind == CK_PERSITE ||
+        a.kind == CK_PHASE || a.nx >= (int64_t(1) << 30))
+        return false;
+    return a.ndim == 1 || (a.ny + gt_y<P>() - 1) / gt_y<P>() <= 65535;
 }
 
 template <int P>
 cudaError_t generic_t(const StepGenericArgs &a, const void *coinp, cudaStream_t s) {
     const auto &cp = *static_cast<const CoinP<typename St<P>::real> *>(coinp);
+    if (generic_tile_ok<P>(a) && a.ndim == 1) {
+        GenGeom g{a.ndim, a.nx, a.ny, a.nx * a.ny, a.shift, a.bc, a.links, a.rthr, a.rk0, a.rk1, a.rstep};
+        const unsigned grid = (unsigned)((a.nx + GT1_X - 1) / GT1_X);
+        const auto gain = real_from_double<typename St<P>::real>(a.gain);
+        if (a.shift == QW_SHIFT_MOVING)
+            k_step_generic_tile1d<P, QW_SHIFT_MOVING><<<grid, GT_THREADS, 0, s>>>(a.in, a.out, g, cp, gain);
+        else
+            k_step_generic_tile1d<P, QW_SHIFT_FLIPFLOP><<<grid, GT_THREADS, 0, s>>>(a.in, a.out, g, cp, gain);
+        return cudaGetLastError();
+    }
     if (generic_tile_ok<P>(a)) {
         GenGeom g{a.ndim, a.nx, a.ny, a.nx * a.ny, a.shift, a.bc, a.links, a.rthr, a.rk0, a.rk1, a.rstep};
         const dim3 grid((unsigned)((a.nx + GT_X - 1) / GT_X), (unsigned)((a.ny + gt_y<P>() - 1) / gt_y<P>()));

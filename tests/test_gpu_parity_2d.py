@@ -237,3 +237,25 @@ def test_tiled_generic_step_multi_tile(qw, prec, bc, shift, dims):
         w.step_adjoint(T)
         assert maxabs(w.state(), psi0) < 2 * amp_tol(prec, T)
     w.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("bc", [0, 1, 2])
+@pytest.mark.parametrize("shift", [0, 1])
+@pytest.mark.parametrize("N", [3 * 1024 + 77, 1024, 5])
+def test_tiled_generic_step_cycle(qw, prec, bc, shift, N):
+    """The tiled generic step on the cycle (1024 sites per block, one-site halo):
+    several tiles, a ragged last one, wrap-around, a fixed mask and links broken
+    at random per step, against the oracle."""
+    rng = np.random.default_rng(N + 7 * bc + 3 * shift)
+    C = inputs.random_unitary(2, rng)
+    fixed = (rng.uniform(size=(1, N)) < 0.1).astype(np.uint8)
+    psi0 = inputs.random_state((2, N), seed=29)
+    T, seed, p = 13, 98, 0.2
+    masks = oracle.link_masks((N,), seed, p, 0, T) | fixed[None]
+    want = oracle.evolve(psi0, C, T, shift=shift, bc=bc, closed=masks, closed_per_step=True)
+    w = qw.Walk((N,), prec=prec, shift=shift, bc=bc).set_coin(C).set_links(fixed).set_link_noise(p, seed)
+    w.set_state(psi0)
+    w.step(T)
+    assert maxabs(w.state(), want) < amp_tol(prec, T)
+    w.close()
