@@ -198,7 +198,11 @@ k_step_generic(View in, View out, GenGeom g, int adjoint, CoinP<typename St<P>::
 // k_step_generic evaluates the coin row and the link again for every output.
 constexpr int GT_X = 64, GT_THREADS = 256;
 template <int P>
-constexpr int gt_y() { return sizeof(Cx<typename St<P>::real>) > 8 ? 8 : 16; }
+constexpr int gt_y() { return 8; }
+// blocks per SM the register budget is sized for: 8 (all 64 warps) for 8-byte
+// amplitudes, whose 64 x 8 tile takes 21 KB of shared memory; 4 for 16-byte ones
+template <int P>
+constexpr int gt_min_blocks() { return sizeof(Cx<typename St<P>::real>) > 8 ? 4 : 8; }
 
 // state of the link from (lx, ly) to its +axis neighbour: 0 open, 1 closed
 // (reflect), 2 absorbed (line boundary); `rnd` is the site's random draw
@@ -213,7 +217,7 @@ __device__ __forceinline__ unsigned char link_state(const GenGeom &g, int axis, 
 }
 
 template <int P, int SHIFT>
-__global__ void __launch_bounds__(GT_THREADS)
+__global__ void __launch_bounds__(GT_THREADS, gt_min_blocks<P>())
 k_step_generic_tile(View in, View out, GenGeom g, CoinP<typename St<P>::real> cp, typename St<P>::real gain) {
     using real = typename St<P>::real;
     using S = St<P>;

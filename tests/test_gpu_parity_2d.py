@@ -217,7 +217,7 @@ def test_diagonal_hadamard_factorises_on_gpu(qw):
 @pytest.mark.parametrize("shift", [0, 1])
 @pytest.mark.parametrize("dims", [(200, 37), (129, 70), (3, 5)])
 def test_tiled_generic_step_multi_tile(qw, prec, bc, shift, dims):
-    """The tiled generic step (64 x 16 or 64 x 8 sites per block, one-site halo
+    """The tiled generic step (64 x 8 sites per block, one-site halo
     in shared memory): several tiles with ragged edges, wrap-around, a fixed
     mask and links broken at random per step, against the oracle; the adjoint
     (the per-site kernel) undoes it."""
