@@ -171,10 +171,19 @@ def cpu_oracle_sample(target_s=12.0):
     t0 = time.perf_counter()
     oracle.evolve(psi, C, steps, openmp=True)
     dt = time.perf_counter() - t0
+    # the small configuration in full on one core: the Hadamard walk on the
+    # cycle of 2001 sites from |0> (x) (|0> + i|1>)/sqrt2, T = 1000
+    psi_s = inputs.localized_1d(2001, 1000)
+    t0 = time.perf_counter()
+    oracle.evolve(psi_s, inputs.hadamard(), 1000)
+    ds = time.perf_counter() - t0
     return {"value": 2.0 * n * steps / dt, "unit": UNIT, "cores": oracle.num_threads(True),
             "kind": "oracle",
             "sample": f"FP64 oracle (C, OpenMP) on a cycle of 2^22 sites, same coin and state "
-                      f"recipe, {steps} steps in {dt:.2f} s"}
+                      f"recipe, {steps} steps in {dt:.2f} s",
+            "single_core_small_config": {
+                "workload": "Hadamard walk, cycle N=2001, T=1000, FP64 oracle, one core, in full",
+                "seconds": ds, "value": 2.0 * 2001 * 1000 / ds, "unit": UNIT}}
 
 
 # ------------------------------------------------------------------ GPU arm
