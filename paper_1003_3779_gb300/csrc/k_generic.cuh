@@ -189,7 +189,8 @@ k_step_generic(View in, View out, GenGeom g, int adjoint, CoinP<typename St<P>::
 
 // ---------------------------------------------------------------------------
 // The common generic case in 2D tiles: forward step, moving or flip-flop shift,
-// one global coin, any boundary, fixed and/or random link masks.  A block owns
+// one global coin, per-site matrices or phase coins, any boundary, fixed and/or
+// random link masks.  A block owns
 // GT_X x gt_y<P>() sites.  It computes phi = C psi once for them and a one-site
 // halo into shared memory, and the state of every link the tile needs once (a
 // site's +x and +y links from one Philox draw), then each site pulls its four
@@ -200,9 +201,11 @@ constexpr int GT_X = 64, GT_THREADS = 256;
 template <int P>
 constexpr int gt_y() { return 8; }
 // blocks per SM the register budget is sized for: 8 (all 64 warps) for 8-byte
-// amplitudes, whose 64 x 8 tile takes 21 KB of shared memory; 4 for 16-byte ones
-template <int P>
-constexpr int gt_min_blocks() { return sizeof(Cx<typename St<P>::real>) > 8 ? 4 : 8; }
+// amplitudes and one global coin, whose 64 x 8 tile takes 21 KB of shared
+// memory; 4 for 16-byte amplitudes and for per-site or phase coins (which need
+// more than 32 registers)
+template <int P, int CK>
+constexpr int gt_min_blocks() { return (sizeof(Cx<typename St<P>::real>) > 8 || CK != CK_COMPLEX) ? 4 : 8; }
 
 // state of the link from (lx, ly) to its +axis neighbour: 0 open, 1 closed
 // (reflect), 2 absorbed (line boundary); `rnd` is the site's random draw
@@ -216,9 +219,11 @@ __device__ __forceinline__ unsigned char link_state(const GenGeom &g, int axis, 
     return (edge && g.bc == QW_BC_LINE) ? 2 : 0;
 }
 
-template <int P, int SHIFT>
-__global__ void __launch_bounds__(GT_THREADS, gt_min_blocks<P>())
-k_step_generic_tile(View in, View out, GenGeom g, CoinP<typename St<P>::real> cp, typename St<P>::real gain) {
+template <int P, int SHIFT, int CK>
+__global__ void __launch_bounds__(GT_THREADS, gt_min_blocks<P, CK>())
+k_step_generic_tile(View in, View out, GenGeom g, CoinP<typename St<P>::real> cp,
+                    const Cx<typename St<P>::real> *__restrict__ coins, const float *__restrict__ phi,
+                    typename St<P>::real gain) {
     using real = typename St<P>::real;
     using S = St<P>;
     using C = Cx<real>;
@@ -234,14 +239,15 @@ k_step_generic_tile(View in, View out, GenGeom g, CoinP<typename St<P>::real> cp
         gx = gx < 0 ? gx + nx : (gx >= nx ? gx % nx : gx);
         gy = gy < 0 ? gy + ny : (gy >= ny ? gy % ny : gy);
         const int64_t u = (int64_t)gy * nx + gx;
-        C a[4];
+        C a[4], e[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) a[k] = S::ld(in, k, u);
+        if (CK == CK_PHASE) gen_phases<real>(phi, u, 4, e);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             C val = czero<real>();
 #pragma unroll
-            for (int k = 0; k < 4; ++k) val = cfma(C{cp.re[r * 4 + k], cp.im[r * 4 + k]}, a[k], val);
+            for (int k = 0; k < 4; ++k) val = cfma(gen_entry<CK, real>(cp, coins, e, 4, u, r, k), a[k], val);
             ph[r][ey][ex] = val;
         }
         if (ex <= GT_X && ey <= GY) {
@@ -285,9 +291,11 @@ k_step_generic_tile(View in, View out, GenGeom g, CoinP<typename St<P>::real> cp
 // its draw.
 constexpr int GT1_X = 1024;
 
-template <int P, int SHIFT>
+template <int P, int SHIFT, int CK>
 __global__ void __launch_bounds__(GT_THREADS)
-k_step_generic_tile1d(View in, View out, GenGeom g, CoinP<typename St<P>::real> cp, typename St<P>::real gain) {
+k_step_generic_tile1d(View in, View out, GenGeom g, CoinP<typename St<P>::real> cp,
+                      const Cx<typename St<P>::real> *__restrict__ coins, const float *__restrict__ phi,
+                      typename St<P>::real gain) {
     using real = typename St<P>::real;
     using S = St<P>;
     using C = Cx<real>;
@@ -300,11 +308,13 @@ k_step_generic_tile1d(View in, View out, GenGeom g, CoinP<typename St<P>::real> 
         int gx = x0 - 1 + ex;
         gx = gx < 0 ? gx + nx : (gx >= nx ? gx % nx : gx);
         const C a0 = S::ld(in, 0, gx), a1 = S::ld(in, 1, gx);
+        C e[2];
+        if (CK == CK_PHASE) gen_phases<real>(phi, gx, 2, e);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             C val = czero<real>();
-            val = cfma(C{cp.re[r * 2], cp.im[r * 2]}, a0, val);
-            val = cfma(C{cp.re[r * 2 + 1], cp.im[r * 2 + 1]}, a1, val);
+            val = cfma(gen_entry<CK, real>(cp, coins, e, 2, gx, r, 0), a0, val);
+            val = cfma(gen_entry<CK, real>(cp, coins, e, 2, gx, r, 1), a1, val);
             ph[r][ex] = val;
         }
         if (ex <= GT1_X) {

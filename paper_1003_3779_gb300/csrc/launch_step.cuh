@@ -256,38 +256,45 @@ static void gogen(const StepGenericArgs &a, const CoinP<typename St<P>::real> &c
         real_from_double<typename St<P>::real>(a.gain));
 }
 
-// The tiled form serves the forward 2D step with one global coin on the axis
-// lattice (any boundary, fixed and random links); the grid's y extent limits
-// ny to 65535 tiles.
+// The tiled forms serve the forward step on the axis lattice (1D and 2D; any
+// coin, boundary and links); the grid's y extent limits ny to 65535 tiles.
 template <int P>
 static bool generic_tile_ok(const StepGenericArgs &a) {
-    if (a.adjoint || !(a.shift == QW_SHIFT_MOVING || a.shift == QW_SHIFT_FLIPFLOP) || a.kind == CK_PERSITE ||
-        a.kind == CK_PHASE || a.nx >= (int64_t(1) << 30))
+    if (a.adjoint || !(a.shift == QW_SHIFT_MOVING || a.shift == QW_SHIFT_FLIPFLOP) || a.nx >= (int64_t(1) << 30))
         return false;
     return a.ndim == 1 || (a.ny + gt_y<P>() - 1) / gt_y<P>() <= 65535;
+}
+
+template <int P, int CK>
+static void gotile(const StepGenericArgs &a, const CoinP<typename St<P>::real> &cp, cudaStream_t s) {
+    using real = typename St<P>::real;
+    GenGeom g{a.ndim, a.nx, a.ny, a.nx * a.ny, a.shift, a.bc, a.links, a.rthr, a.rk0, a.rk1, a.rstep};
+    const auto gain = real_from_double<real>(a.gain);
+    const auto *coins = static_cast<const Cx<real> *>(a.coins);
+    if (a.ndim == 1) {
+        const unsigned grid = (unsigned)((a.nx + GT1_X - 1) / GT1_X);
+        if (a.shift == QW_SHIFT_MOVING)
+            k_step_generic_tile1d<P, QW_SHIFT_MOVING, CK><<<grid, GT_THREADS, 0, s>>>(a.in, a.out, g, cp, coins, a.phi, gain);
+        else
+            k_step_generic_tile1d<P, QW_SHIFT_FLIPFLOP, CK><<<grid, GT_THREADS, 0, s>>>(a.in, a.out, g, cp, coins, a.phi, gain);
+        return;
+    }
+    const dim3 grid((unsigned)((a.nx + GT_X - 1) / GT_X), (unsigned)((a.ny + gt_y<P>() - 1) / gt_y<P>()));
+    if (a.shift == QW_SHIFT_MOVING)
+        k_step_generic_tile<P, QW_SHIFT_MOVING, CK><<<grid, GT_THREADS, 0, s>>>(a.in, a.out, g, cp, coins, a.phi, gain);
+    else
+        k_step_generic_tile<P, QW_SHIFT_FLIPFLOP, CK><<<grid, GT_THREADS, 0, s>>>(a.in, a.out, g, cp, coins, a.phi, gain);
 }
 
 template <int P>
 cudaError_t generic_t(const StepGenericArgs &a, const void *coinp, cudaStream_t s) {
     const auto &cp = *static_cast<const CoinP<typename St<P>::real> *>(coinp);
-    if (generic_tile_ok<P>(a) && a.ndim == 1) {
-        GenGeom g{a.ndim, a.nx, a.ny, a.nx * a.ny, a.shift, a.bc, a.links, a.rthr, a.rk0, a.rk1, a.rstep};
-        const unsigned grid = (unsigned)((a.nx + GT1_X - 1) / GT1_X);
-        const auto gain = real_from_double<typename St<P>::real>(a.gain);
-        if (a.shift == QW_SHIFT_MOVING)
-            k_step_generic_tile1d<P, QW_SHIFT_MOVING><<<grid, GT_THREADS, 0, s>>>(a.in, a.out, g, cp, gain);
-        else
-            k_step_generic_tile1d<P, QW_SHIFT_FLIPFLOP><<<grid, GT_THREADS, 0, s>>>(a.in, a.out, g, cp, gain);
-        return cudaGetLastError();
-    }
     if (generic_tile_ok<P>(a)) {
-        GenGeom g{a.ndim, a.nx, a.ny, a.nx * a.ny, a.shift, a.bc, a.links, a.rthr, a.rk0, a.rk1, a.rstep};
-        const dim3 grid((unsigned)((a.nx + GT_X - 1) / GT_X), (unsigned)((a.ny + gt_y<P>() - 1) / gt_y<P>()));
-        const auto gain = real_from_double<typename St<P>::real>(a.gain);
-        if (a.shift == QW_SHIFT_MOVING)
-            k_step_generic_tile<P, QW_SHIFT_MOVING><<<grid, GT_THREADS, 0, s>>>(a.in, a.out, g, cp, gain);
-        else
-            k_step_generic_tile<P, QW_SHIFT_FLIPFLOP><<<grid, GT_THREADS, 0, s>>>(a.in, a.out, g, cp, gain);
+        switch (a.kind) {
+            case CK_PERSITE: gotile<P, CK_PERSITE>(a, cp, s); break;
+            case CK_PHASE: gotile<P, CK_PHASE>(a, cp, s); break;
+            default: gotile<P, CK_COMPLEX>(a, cp, s); break;   // every global coin as a full matrix
+        }
         return cudaGetLastError();
     }
     switch (a.kind) {

@@ -215,6 +215,39 @@ def test_diagonal_hadamard_factorises_on_gpu(qw):
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("bc", [0, 1, 2])
 @pytest.mark.parametrize("shift", [0, 1])
+@pytest.mark.parametrize("dims", [(200, 37), (3, 5)])
+@pytest.mark.parametrize("coin", ["per_site", "phase"])
+def test_tiled_generic_step_site_coins(qw, prec, bc, shift, dims, coin):
+    """The tiled generic step with per-site matrices or phase coins, several
+    tiles, boundaries and both kinds of broken links, against the oracle."""
+    Lx, Ly = dims
+    ns = Lx * Ly
+    rng = np.random.default_rng(Lx + 5 * bc + 3 * shift + len(coin))
+    fixed = (rng.uniform(size=(2, ns)) < 0.1).astype(np.uint8)
+    psi0 = inputs.random_state((4, Ly, Lx), seed=30)
+    T, seed, p = 9, 97, 0.2
+    masks = oracle.link_masks((Ly, Lx), seed, p, 0, T) | fixed[None]
+    w = qw.Walk((Lx, Ly), prec=prec, shift=shift, bc=bc)
+    tol = amp_tol(prec, T)
+    if coin == "per_site":
+        coins = np.stack([inputs.random_unitary(4, rng) for _ in range(ns)])
+        want = oracle.evolve(psi0, coins, T, shift=shift, bc=bc, closed=masks, closed_per_step=True)
+        w.set_coin(coins, per_site=True)
+    else:
+        phi = rng.uniform(-0.5, 0.5, size=(ns, 4)).astype(np.float32)
+        want = oracle.evolve(psi0, inputs.grover(), T, shift=shift, bc=bc, phi=phi.astype(np.float64),
+                             closed=masks, closed_per_step=True)
+        w.set_coin_phases(inputs.grover(), phi)
+        tol += T * 2e-7 if prec in ("f32", "bf16") else 0
+    w.set_links(fixed).set_link_noise(p, seed).set_state(psi0)
+    w.step(T)
+    assert maxabs(w.state(), want) < tol
+    w.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("bc", [0, 1, 2])
+@pytest.mark.parametrize("shift", [0, 1])
 @pytest.mark.parametrize("dims", [(200, 37), (129, 70), (3, 5)])
 def test_tiled_generic_step_multi_tile(qw, prec, bc, shift, dims):
     """The tiled generic step (64 x 8 sites per block, one-site halo
