@@ -210,6 +210,24 @@ def test_link_masks_rate_and_independence():
     assert oracle.link_masks(shape, seed=1, p=1.0, t0=0, T=1).all()
 
 
+def test_link_masks_draw_words_from_the_known_answer_vector():
+    """The mask of site 0 at step 0 with seed 0 comes from counter (0, 0, 0, 0)
+    and key (0, 0), whose published Philox4x32-10 output starts 6627e8d5
+    e169c58d: the x-link takes word 0 and the y-link word 1, each closed exactly
+    when the threshold floor(p 2^32) exceeds its word."""
+    rows = [ln.split() for ln in open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    zero = [r for r in rows if all(int(x, 16) == 0 for x in r[:6])][0]
+    words = [int(zero[6], 16), int(zero[7], 16)]
+    for axis, wd in enumerate(words):
+        at = oracle.link_masks((1, 1), seed=0, p=wd / 2.0 ** 32, t0=0, T=1)[0, axis, 0]
+        above = oracle.link_masks((1, 1), seed=0, p=(wd + 1) / 2.0 ** 32, t0=0, T=1)[0, axis, 0]
+        assert (at, above) == (0, 1), axis
+    # on the cycle the single link of a site is word 0
+    assert oracle.link_masks((1,), seed=0, p=(words[0] + 1) / 2.0 ** 32, t0=0, T=1)[0, 0, 0] == 1
+    assert oracle.link_masks((1,), seed=0, p=words[0] / 2.0 ** 32, t0=0, T=1)[0, 0, 0] == 0
+
+
 # ------------------------------------------------------------ invariants
 def test_norm_every_step_and_reversibility():
     rng = np.random.default_rng(51)
