@@ -220,6 +220,27 @@ def ncu_traffic(kernel="k_step1d_sweep", tile=None):
     return float(b.group(1))
 
 
+def graph_cpu_sample(target_s=4.0):
+    """The FP64 graph oracle (OpenMP, all host cores) on a bounded sample of the
+    random 4-regular workload: 2^20 vertices, as many steps as fit in ~target_s."""
+    import oracle
+    from paper_1003_3779_gb300 import inputs
+    nv = 1 << 20
+    off, partner = inputs.random_regular_arcs(nv, 4, seed=5)
+    psi = inputs.random_state((int(off[-1]),), seed=6)
+    oracle.graph_evolve(off, partner, psi, 1, openmp=True)     # warm-up / page-in
+    t0 = time.perf_counter()
+    oracle.graph_evolve(off, partner, psi, 1, openmp=True)
+    t1 = time.perf_counter() - t0
+    steps = max(1, min(32, int(target_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.graph_evolve(off, partner, psi, steps, openmp=True)
+    dt = time.perf_counter() - t0
+    return {"value": float(off[-1]) * steps / dt, "unit": "arc-updates/s", "cores": oracle.num_threads(True),
+            "kind": "oracle", "sample": f"FP64 graph oracle (C, OpenMP), random 4-regular graph with 2^20 "
+                                        f"vertices, {steps} steps in {dt:.2f} s"}
+
+
 def graph_timing(qw, _in, make, stream, hbm_gbs, steps=20):
     """One graph workload: build it, autotune the kernel form, time `steps` walk
     steps with CUDA events on the launching stream, check the norm."""
@@ -559,6 +580,8 @@ def run_gpu(args, rank, world, local):
         for gname, make in (("random_4_regular_2e26", lambda: _in.random_regular_arcs(1 << 26, 4, seed=5)),
                             ("torus_8192_as_graph", lambda: _in.lattice_graph_arcs(8192, 8192))):
             graph_leg[gname] = graph_timing(qw, _in, make, stream, hbm_gbs)
+        if not args.skip_cpu:
+            graph_leg["random_4_regular_2e26"]["cpu_baseline"] = graph_cpu_sample()
 
     forms, accuracy = {}, {}
     if rank == 0 and not args.skip_forms:
