@@ -677,16 +677,19 @@ qw_status qw_get_state(qw_walk *w, void *amp_out, qw_cdtype dtype, int on_device
 
 qw_status qw_step(qw_walk *w, int64_t T) {
     if (!w) return QW_EINVAL;
+    NvtxRange nvtx("qw_step");
     return run_steps(w, T, 0);
 }
 
 qw_status qw_step_adjoint(qw_walk *w, int64_t T) {
     if (!w) return QW_EINVAL;
+    NvtxRange nvtx("qw_step_adjoint");
     return run_steps(w, T, 1);
 }
 
 qw_status qw_probabilities(qw_walk *w, void *P_out, qw_rdtype pdtype, int on_device, double *norm_out) {
     if (!w) return QW_EINVAL;
+    NvtxRange nvtx("qw_probabilities");
     if (pdtype != QW_R64 && pdtype != QW_R32) return set_error(w, QW_EINVAL, "bad probability dtype");
     const size_t pb = (size_t)w->ns * (pdtype == QW_R32 ? 4 : 8);
     void *pdst = nullptr;
@@ -726,6 +729,7 @@ qw_status qw_probabilities(qw_walk *w, void *P_out, qw_rdtype pdtype, int on_dev
 qw_status qw_run_host_batch(qw_walk *w, int count, const void *amp_in, int64_t in_stride, qw_cdtype dtype, int64_t T,
                             void *P_out, int64_t p_stride, qw_rdtype pdtype, double *norms_out) {
     if (!w) return QW_EINVAL;
+    NvtxRange nvtx("qw_run_host_batch");
     if (count < 0 || T < 0 || in_stride < 0 || p_stride < 0 || (count && (!amp_in || !P_out)) ||
         (pdtype != QW_R64 && pdtype != QW_R32))
         return set_error(w, QW_EINVAL, "bad count, T, strides, buffers or probability dtype");

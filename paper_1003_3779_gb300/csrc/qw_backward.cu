@@ -173,6 +173,7 @@ using namespace qw;
 extern "C" qw_status qw_backward(qw_walk *w, const int64_t rect[4], int64_t T, int64_t K, double *loss_out,
                                  double *grad_phi, int on_device) {
     if (!w) return QW_EINVAL;
+    NvtxRange nvtx("qw_backward");
     if (!rect || !grad_phi || T < 0 || K < 1) return set_error(w, QW_EINVAL, "bad rect, grad buffer, T or K");
     if (w->ndim != 2) return set_error(w, QW_EUNSUPPORTED, "qw_backward is defined on the torus");
     if (w->kind != CK_PHASE) return set_error(w, QW_ESTATE, "qw_backward needs a phase coin (qw_set_coin_phases)");

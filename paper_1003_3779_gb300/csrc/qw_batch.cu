@@ -641,6 +641,7 @@ qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T, const 
 
 qw_status qw_batch_step(qw_batch *b) {
     if (!b) return QW_EINVAL;
+    NvtxRange nvtx("qw_batch_step");
     cudaError_t e;
     if (!b->exec) {
         e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);

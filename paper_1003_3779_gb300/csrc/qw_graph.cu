@@ -796,11 +796,13 @@ qw_status qw_gwalk_get_state(qw_gwalk *g, void *amp_out, qw_cdtype dtype, int on
 
 qw_status qw_gwalk_step(qw_gwalk *g, int64_t T) {
     if (!g) return QW_EINVAL;
+    NvtxRange nvtx("qw_gwalk_step");
     return run_graph(g, T, 0);
 }
 
 qw_status qw_gwalk_step_adjoint(qw_gwalk *g, int64_t T) {
     if (!g) return QW_EINVAL;
+    NvtxRange nvtx("qw_gwalk_step_adjoint");
     return run_graph(g, T, 1);
 }
 

@@ -73,6 +73,20 @@ struct qw_walk {
     std::string err;
 };
 
+// NVTX ranges around the public calls that launch work, for timelines in a
+// profiler; header-only, and nothing happens when no tool is attached
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+#else
+struct NvtxRange {
+    explicit NvtxRange(const char *) {}
+};
+#endif
+
 namespace qw {
 
 qw_status set_error(qw_walk *w, qw_status st, const std::string &msg);
