@@ -322,7 +322,7 @@ qw_status qw_gwalk_probabilities(qw_gwalk *g, void *P_out, qw_rdtype pdtype, int
  * computes the coin and writes bucket runs, the second permutes within one
  * L2-resident window by scattered writes (2) or gathered reads (3)); -1
  * restores the default (push).  Every form gives the same bits.  Forms 2 and 3
- * build tables on first use (host work O(arcs); device memory 10 bytes per arc
+ * build tables on first use (host work O(arcs); device memory 14 bytes per arc
  * plus one more state buffer). */
 qw_status qw_gwalk_set_variant(qw_gwalk *g, int variant);
 
