@@ -47,7 +47,8 @@ THETA = math.pi / 4
 SEED = 1
 WORKLOAD = "1D SU(2) walk, cycle N=2^27, theta=pi/4, T=4096, random normalised complex64 state (seed 1)"
 
-SMS, FP32_LANES = 152, 128
+FP32_LANES = 128            # FP32 lanes per SM (Blackwell)
+SMS = None                  # read from the device (cudaDevAttrMultiProcessorCount) in run_gpu
 
 
 def load_peaks():
@@ -241,6 +242,55 @@ def graph_cpu_sample(target_s=4.0):
                                         f"vertices, {steps} steps in {dt:.2f} s"}
 
 
+def batch_oracle_sample(Nb, Tb, coins, x0b, cs):
+    """CPU baseline of the batched workload: the FP64 oracle (OpenMP) run on a
+    fixed sample of its walks -- every walk whose coin lies within 2e-3 of
+    diagonal (theta near 0 or pi/2, where float rounding is biased), the longest
+    cycle, the longest walk and four seeded others -- each on its light-cone
+    window.  Returns the timing and the oracle's P of each sampled walk, against
+    which the GPU forms' per-walk L1 is reported."""
+    import oracle
+    from paper_1003_3779_gb300 import inputs
+    theta = np.array([math.atan2(abs(c[0, 1]), abs(c[0, 0])) for c in coins])
+    near = [int(i) for i in np.where(np.minimum(theta, math.pi / 2 - theta) < 2e-3)[0]]
+    rng = np.random.default_rng(12)
+    sample = sorted(set(near + [int(np.argmax(Nb)), int(np.argmax(Tb))] +
+                        [int(i) for i in rng.choice(len(Nb), 4, replace=False)]))
+    ref, units = {}, 0.0
+    t0 = time.perf_counter()
+    for i in sample:
+        n, t, x = int(Nb[i]), int(Tb[i]), int(x0b[i])
+        if 2 * t + 1 < n:       # the light-cone window, placed back on the cycle
+            m = 2 * t + 1
+            out = oracle.evolve(inputs.localized_1d(m, t, cs), coins[i], t, openmp=True)
+            P = np.zeros(n)
+            P[(x - t + np.arange(m)) % n] = (np.abs(out) ** 2).sum(axis=0)
+            units += 2.0 * m * t
+        else:
+            out = oracle.evolve(inputs.localized_1d(n, x, cs), coins[i], t, openmp=True)
+            P = (np.abs(out) ** 2).sum(axis=0)
+            units += 2.0 * n * t
+        ref[i] = P
+    dt = time.perf_counter() - t0
+    return ({"value": units / dt, "unit": UNIT, "cores": oracle.num_threads(True), "kind": "oracle",
+             "sample": f"FP64 oracle (C, OpenMP) on {len(sample)} of the 4096 walks (all {len(near)} "
+                       f"with theta within 2e-3 of 0 or pi/2, the longest cycle, the longest walk, four "
+                       f"seeded others), each on its light-cone window, in {dt:.2f} s",
+             "walks": sample, "near_diagonal_walks": near}, ref)
+
+
+def batch_l1(P, offsets, ref, near):
+    """Per-walk L1 and max-abs of the batch's P against the oracle sample."""
+    l1s, mx = {}, 0.0
+    for i, Pw in ref.items():
+        d = np.abs(P[offsets[i]:offsets[i + 1]].astype(np.float64) - Pw)
+        l1s[i] = float(d.sum())
+        mx = max(mx, float(d.max()))
+    return {"max_l1": max(l1s.values()), "max_l1_near_diagonal": max((l1s[i] for i in near), default=None),
+            "max_l1_others": max((v for i, v in l1s.items() if i not in near), default=None),
+            "maxabs_p": mx, "walks_over_1e-4": sorted(int(i) for i, v in l1s.items() if v >= 1e-4)}
+
+
 def graph_timing(qw, _in, make, stream, hbm_gbs, steps=20):
     """One graph workload: build it, autotune the kernel form, time `steps` walk
     steps with CUDA events on the launching stream, check the norm."""
@@ -273,6 +323,52 @@ def graph_timing(qw, _in, make, stream, hbm_gbs, steps=20):
             "norm_err": abs(norm - 1.0)}
 
 
+# Instructions on the FP32 pipe per site-step of each coin class (2x2 coin on
+# complex amplitudes): the Hadamard class adds (4 FADD), a real coin multiplies
+# and accumulates (4 FMUL + 4 FFMA), a complex coin does a complex
+# multiply-accumulate per entry (16 FMUL / FFMA).  Flops count an FFMA as 2.
+COIN_CLASS_WORK = {"hadamard_class": (4, 4.0, "FADD"), "real": (8, 12.0, "FMUL/FFMA"),
+                   "complex": (16, 28.0, "FMUL/FFMA")}
+
+
+def coin_class_leg(qw, C, dev0, stream, sm_max_mhz, hbm_gbs):
+    """The benchmark workload (N = 2^27, T = 4096, FP32, same state) with another
+    SU(2) coin: autotuned plan, CUDA events around qw_step, and the kernel's
+    roofline against the FP32 instruction issue rate of its coin class."""
+    import torch
+    w = qw.Walk((N_SITES,), prec="f32").set_coin(C).set_state(dev0)
+    tune = json.loads(w.autotune())
+    K, tile, var = w.plan_ex()
+    desc = w.describe()
+    qw.qw_set_state(w.h, dev0)
+    qw.qw_step(w.h, 2 * K)
+    qw.qw_set_state(w.h, dev0)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    qw.qw_step(w.h, T_STEPS)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    norm = w.norm()
+    w.close()
+    inst, flops, op = COIN_CLASS_WORK[desc["coin_kind"]]
+    launches = math.ceil(T_STEPS / K)
+    issue_peak = SMS * FP32_LANES * sm_max_mhz * 1e6            # FP32 instructions / s
+    ach_inst = inst * N_SITES * T_STEPS / t
+    return {"site_coin_updates_per_s": 2.0 * N_SITES * T_STEPS / t, "ms_per_T_steps": t * 1e3,
+            "coin_kind": desc["coin_kind"], "kernel": desc["path"], "k": K, "tile": tile,
+            "avg_launch_ms": t * 1e3 / launches, "norm_err": abs(norm - 1.0), "autotune": tune,
+            "roofline": {"bound": "alu", "achieved": ach_inst / 1e12, "peak": issue_peak / 1e12,
+                         "unit": "T FP32-instructions/s", "frac": ach_inst / issue_peak,
+                         "instructions_per_site_step": inst, "op": op,
+                         "achieved_tflops": flops * N_SITES * T_STEPS / t / 1e12,
+                         "peak_source": f"{SMS} SMs (device attribute) x {FP32_LANES} FP32 lanes x "
+                                        f"{sm_max_mhz:.0f} MHz (derived)",
+                         "hbm_view": {"effective_bytes_per_site_step": 32.0 / (T_STEPS / launches),
+                                      "achieved_gbs": 32.0 * N_SITES * launches / t / 1e9,
+                                      "frac": 32.0 * N_SITES * launches / t / 1e9 / hbm_gbs}}}
+
+
 def run_gpu(args, rank, world, local):
     import torch
     import paper_1003_3779_gb300.qw as qw
@@ -281,6 +377,8 @@ def run_gpu(args, rank, world, local):
     torch.cuda.set_device(local)
     dist = init_dist(world, "nccl")
     hbm_gbs, sm_max_mhz, peak_src = load_peaks()
+    global SMS
+    SMS = torch.cuda.get_device_properties(local).multi_processor_count
     stream = torch.cuda.current_stream()
 
     global N_SITES
@@ -353,8 +451,8 @@ def run_gpu(args, rank, world, local):
     if alu_frac >= hbm_frac:
         roof = {"bound": "alu", "achieved": ach_tflops, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": alu_frac, "traffic": traffic,
-                "peak_source": f"152 SMs x 128 FP32 lanes x {flops_per_lane_clk} flop ({op}) x "
-                               f"{sm_max_mhz:.0f} MHz (derived)",
+                "peak_source": f"{SMS} SMs (device attribute) x 128 FP32 lanes x {flops_per_lane_clk} flop "
+                               f"({op}) x {sm_max_mhz:.0f} MHz (derived)",
                 "hbm_view": {"achieved_gbs": ach_gbs, "peak_gbs": hbm_gbs, "frac": hbm_frac,
                              "peak_source": f"{peak_src} HBM copy"}}
     else:
@@ -512,7 +610,18 @@ def run_gpu(args, rank, world, local):
             "frac_of_measured": 32.0 * N_SITES / ts / 1e9 / hbm_gbs, "norm": ws.norm()}
         ws.close()
 
-    # batched walks: 4096 walks in one persistent launch (graph replay), FP32 and bf16 storage
+    # the other SU(2) coin classes on the benchmark workload: a real rotation and a
+    # complex coin (the headline's theta = pi/4 is the Hadamard class)
+    coin_classes = {}
+    if rank == 0 and not args.skip_forms:
+        from paper_1003_3779_gb300 import inputs as _in
+        for cname, Cc in (("real_theta_0.3", _in.su2(0.3)), ("complex_theta_pi4_xi_0.3_zeta_-0.2",
+                                                            _in.su2(THETA, 0.3, -0.2))):
+            coin_classes[cname] = coin_class_leg(qw, Cc, dev0, stream, sm_max_mhz, hbm_gbs)
+
+    # batched walks: 4096 walks in one persistent launch (graph replay), FP32,
+    # bf16 storage and double-float, with per-walk L1 against the FP64 oracle on a
+    # sample of the walks (the batch's CPU baseline)
     batch = {}
     if rank == 0 and not args.skip_forms:
         from paper_1003_3779_gb300 import inputs as _in
@@ -521,7 +630,11 @@ def run_gpu(args, rank, world, local):
         dense = float(np.sum(2.0 * Nb * Tb))
         tc = np.minimum(Tb, Nb // 2)
         active = float(np.sum(2.0 * (tc.astype(np.float64) ** 2 + (Tb - tc) * Nb.astype(np.float64))))
-        for pname in ("f32", "bf16"):
+        batch_ref, near = None, []
+        if not args.skip_cpu:
+            batch["cpu_baseline"], batch_ref = batch_oracle_sample(Nb, Tb, coins_b, x0b, _in.BATCH_COIN_STATE)
+            near = batch["cpu_baseline"]["near_diagonal_walks"]
+        for pname in ("f32", "bf16", "comp"):
             bt = qw.Batch(Nb, Tb, coins_b, x0b, _in.BATCH_COIN_STATE, prec=pname)
             tune_b = json.loads(bt.autotune())
             bt.step()
@@ -532,7 +645,7 @@ def run_gpu(args, rank, world, local):
             b.record(stream)
             torch.cuda.synchronize()
             tb = a.elapsed_time(b) / 1e3 / 3
-            _, nb_ = bt.probabilities()
+            Pb_, nb_ = bt.probabilities()
             # the real 2x2 coin is 8 FP32 instructions (4 FMUL, 4 FFMA) per site-step;
             # against the FP32 issue rate over the light-cone (active) site-steps only
             inst_rate = 8.0 * (active / 2.0) / tb / 1e12
@@ -540,10 +653,13 @@ def run_gpu(args, rank, world, local):
             batch[pname] = {"dense_site_coin_updates_per_s": dense / tb,
                             "active_site_coin_updates_per_s": active / tb, "ms_per_batch": tb * 1e3,
                             "k": tune_b["k"], "variant": tune_b.get("variant"), "cta_walks": tune_b.get("cta_walks"),
-                            "alu_view": {"achieved_tinst_per_s": inst_rate, "peak_tinst_per_s": issue_peak,
-                                         "frac": inst_rate / issue_peak,
-                                         "note": "8 FP32 instructions per active site-step (real coin)"},
                             "max_norm_err": float(np.abs(nb_ - 1).max())}
+            if pname != "comp":
+                batch[pname]["alu_view"] = {"achieved_tinst_per_s": inst_rate, "peak_tinst_per_s": issue_peak,
+                                            "frac": inst_rate / issue_peak,
+                                            "note": "8 FP32 instructions per active site-step (real coin)"}
+            if batch_ref is not None:
+                batch[pname]["l1_vs_oracle"] = batch_l1(Pb_, bt.offsets, batch_ref, near)
             bt.close()
 
     # region-mass gradient on the 1024^2 torus (forward with checkpoints + adjoint sweep)
@@ -612,6 +728,25 @@ def run_gpu(args, rank, world, local):
             else:
                 forms[name]["l1_vs_f64"] = float((Pf - ref).abs().sum())
                 forms[name]["maxabs_p_vs_f64"] = float((Pf - ref).abs().max())
+            if name == "bf16":
+                # one step per launch (k = 1), where 16 bytes per site-step against
+                # FP32's 32 halve the HBM traffic of the memory-bound step
+                wf.set_plan(1, 0)
+                qw.qw_set_state(wf.h, dev0)
+                qw.qw_step(wf.h, 8)
+                qw.qw_set_state(wf.h, dev0)
+                a.record(stream)
+                qw.qw_step(wf.h, T_STEPS)
+                b.record(stream)
+                torch.cuda.synchronize()
+                qw.qw_probabilities(wf.h, Pf)
+                t1 = a.elapsed_time(b) / 1e3
+                gbs = 16.0 * N_SITES * T_STEPS / t1 / 1e9
+                forms["bf16_k1"] = {"value": 2.0 * N_SITES * T_STEPS / t1, "unit": UNIT, "k": 1,
+                                    "kernel": wf.describe()["path"], "algorithmic_bytes_per_site_step": 16,
+                                    "hbm_gbs": gbs, "frac_of_measured": gbs / hbm_gbs,
+                                    "l1_vs_f64": float((Pf - ref).abs().sum()),
+                                    "maxabs_p_vs_f64": float((Pf - ref).abs().max())}
             del Pf
             wf.close()
         accuracy = {"l1_vs_f64_gpu": float((P32 - ref).abs().sum()),
@@ -629,6 +764,7 @@ def run_gpu(args, rank, world, local):
         "forms": forms, "accuracy": accuracy, "e2e": e2e, "clocks": clk.summary(), "tune": tune,
         "K": K, "tile": tile, "launches": args.steps * (launches_step + 2), "dist": dist,
         "torus": torus, "batch": batch, "grad": grad_leg, "graph": graph_leg,
+        "coin_classes": coin_classes, "coin_kind": desc["coin_kind"],
     }
 
 
@@ -778,12 +914,16 @@ def main():
         "config": {"workload": WORKLOAD if N_SITES == 1 << 27 else f"{WORKLOAD} (N={N_SITES})",
                    "sites": N_SITES, "coin_dim": 2, "T": T_STEPS,
                    "k": r["K"], "tile": r["tile"], "parallelism": f"replicas{world}",
+                   "coin_class": r["coin_kind"] + " (theta = pi/4 with zero phases is lambda * M, M a "
+                                                  "+-1 matrix: four additions per site-step; the real and "
+                                                  "complex SU(2) classes are in coin_classes)",
                    "l2": "inputs larger than L2 (2 GiB state, 129 MB L2); no flush needed",
                    "step": "set_state (device copy) + T=4096 walk steps + marginals/norm"},
         "clocks": r["clocks"], "e2e": r["e2e"], "gpu_launches": r["launches"],
         "roofline": r["roofline"], "roofline_k1": r["roofline_k1"], "cpu_baseline": cpu,
         "accuracy": r["accuracy"], "forms": r["forms"], "torus_8192": r["torus"],
         "batch_4096": r["batch"], "region_grad_1024": r["grad"], "graph": r["graph"],
+        "coin_classes": r["coin_classes"],
         "norm": r["norm"], "autotune": r["tune"],
     }
     print(json.dumps(out))

@@ -247,10 +247,13 @@ qw_status qw_backward(qw_walk *w, const int64_t rect[4], int64_t T, int64_t K,
  * a NULL amp, nsites < 1, a coin_dim other than 2 or 4, or an unknown dtype
  * return QW_EINVAL before anything is launched.  The first call on a device
  * looks up that array's device address (cudaGetSymbolAddress, with the device
- * current); make that first call before any stream capture.  All calls share
- * the array: each call overwrites the slots it uses, so nothing needs
- * clearing, but two calls that overlap on the GPU (different streams, or
- * different host threads) race on it and must be ordered by the caller.
+ * current) and loads the entry point's three kernels on that device; make that
+ * first call before any stream capture.  The address is kept until the process
+ * exits (a cudaDeviceReset makes it stale, with every other handle of this
+ * library).  All calls share the array: each call overwrites the slots it
+ * uses, so nothing needs clearing, but two calls that overlap on the GPU
+ * (different streams, or different host threads) race on it and must be
+ * ordered by the caller.
  * Returns QW_ECUDA if the lookup or a launch fails. */
 qw_status qw_probabilities_noalloc(const void *amp, qw_cdtype dtype, int coin_dim, int64_t nsites,
                                    void *P_out, qw_rdtype pdtype, double *norm_out,
@@ -346,12 +349,16 @@ const char *qw_gwalk_last_error(const qw_gwalk *g);
  * sites, T[i] steps, its own 2x2 coin (coins + 8*i: row-major complex), and the
  * localised initial state |x0[i]> (x) (coin_state[0]|0> + coin_state[1]|1>)
  * (coin_state: 2 complex = 4 doubles).  prec: QW_F32 or QW_F32_BF16STORE
- * (state storage; arithmetic is float), anything else QW_EUNSUPPORTED.  All
- * arrays are host pointers; QW_EINVAL for N < 1, T < 0 or x0 outside [0, N).
- * Device memory: two state buffers for all walks (ping-pong), their
- * probabilities (float) and norms.  The default kernel (variant 1 of
- * qw_batch_set_plan_ex) sweeps each walk's light cone [x0 - t, x0 + t] only;
- * the state outside it stays exactly zero. */
+ * (state storage; arithmetic is float), or QW_F32_COMP (double-float: the
+ * state, the coin and the arithmetic carry a hi + lo pair of floats, ~48 bits;
+ * for walks whose coin entries lie within ~2^-20 of +-1, where float rounding
+ * is biased; warp tiles of 8 sites per lane, variant 0 only, k <= 64);
+ * anything else QW_EUNSUPPORTED.  All arrays are host pointers; QW_EINVAL for
+ * N < 1, T < 0 or x0 outside [0, N).  Device memory: two state buffers for all
+ * walks (ping-pong; the double-float form holds twice the planes), their
+ * probabilities (float) and norms.  The default kernel of the float forms
+ * (variant 1 of qw_batch_set_plan_ex) sweeps each walk's light cone
+ * [x0 - t, x0 + t] only; the state outside it stays exactly zero. */
 qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T,
                           const double *coins, const int64_t *x0,
                           const double *coin_state, qw_precision prec,
@@ -364,8 +371,8 @@ qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T,
 qw_status qw_batch_step(qw_batch *b);
 
 /* Temporal depth k (steps per round, 1..128; default 96) of the batched
- * kernel; the tile is fixed at 16 sites per lane.  Changing k re-captures the
- * graph. */
+ * kernel; the tile is fixed at 16 sites per lane (double-float: 1..64, default
+ * 32, 8 sites per lane).  Changing k re-captures the graph. */
 qw_status qw_batch_set_plan(qw_batch *b, int depth_k);
 qw_status qw_batch_get_plan(const qw_batch *b, int *depth_k, int *tile);
 
@@ -374,7 +381,8 @@ qw_status qw_batch_get_plan(const qw_batch *b, int *depth_k, int *tile);
  * skipped; 1 = time-skewed window sweep (the sweep of qw_set_plan_ex variant 1
  * over the chunks that cover a walk's light cone, no halo; over the whole
  * cycle with warm-up chunks once the cone nearly covers it).  Both give the
- * same results up to rounding order.  QW_EINVAL for another variant. */
+ * same results up to rounding order.  QW_EINVAL for another variant;
+ * QW_EUNSUPPORTED for variant 1 on a double-float batch. */
 qw_status qw_batch_set_plan_ex(qw_batch *b, int depth_k, int variant);
 qw_status qw_batch_get_plan_ex(const qw_batch *b, int *depth_k, int *tile, int *variant);
 

@@ -172,9 +172,24 @@ static void effective_plan(const qw_walk *w, int &k, int &tile) {
 }
 
 // Global coin: store, classify, and convert to the compute precision.
+//
+// The specialised kernels (Grover, H (x) H, the Hadamard class lambda * M)
+// apply their own matrix, not the caller's.  In float compute a coin within
+// 1e-15 (absolute) or 1e-14 (relative) of one of them rounds to the same
+// float matrix, so the substitution changes nothing.  The double and
+// double-float forms carry the caller's entries to 53 / ~48 bits: there a coin
+// is specialised only when every entry lies within one double ulp of the
+// specialised matrix (|h - 1/2| <= 2^-53; for lambda * M the four magnitudes
+// within 2^-52 relative of their mean).  Such a substitution moves each entry
+// by no more than one rounding, as the arithmetic of a step does anyway; a
+// coin that differs by more runs as given.  (kron(H, H) of the rounded 1/sqrt2,
+// whose entries are 1/2 - 2^-53, and SU(2) at theta = pi/4, whose cos and sin
+// differ by one ulp, stay specialised.)
 static void apply_global_coin(qw_walk *w, const double *h) {
     const int d = w->d, n = d * d;
     std::memcpy(w->coin_host, h, sizeof(double) * 2 * n);
+    const bool wide = w->prec == QW_F64 || w->prec == QW_F32_COMP;
+    const double tol_abs = wide ? 0x1p-53 : 1e-15, tol_rel = wide ? 0x1p-52 : 1e-14;
     bool real = true;
     for (int i = 0; i < n; ++i) real = real && h[2 * i + 1] == 0.0;
     int kind = real ? CK_REAL : CK_COMPLEX;
@@ -184,8 +199,8 @@ static void apply_global_coin(qw_walk *w, const double *h) {
             for (int c = 0; c < 4; ++c) {
                 const double g = (r == c) ? -0.5 : 0.5;
                 const int sgn = ((r & c & 1) ^ ((r >> 1) & (c >> 1) & 1)) ? -1 : 1;  // H(x)H, c = 2j+k
-                grover = grover && std::fabs(h[2 * (4 * r + c)] - g) <= 1e-15;
-                hh = hh && std::fabs(h[2 * (4 * r + c)] - 0.5 * sgn) <= 1e-15;
+                grover = grover && std::fabs(h[2 * (4 * r + c)] - g) <= tol_abs;
+                hh = hh && std::fabs(h[2 * (4 * r + c)] - 0.5 * sgn) <= tol_abs;
             }
         if (grover) kind = CK_GROVER;
         else if (hh) kind = CK_HH;
@@ -214,7 +229,10 @@ static void apply_global_coin(qw_walk *w, const double *h) {
     // rotation / Hadamard-type coins, to first order otherwise): every step scales
     // the norm by alpha.  The kernels divide it back out.  A coin that is not
     // close to unitary (|alpha - 1| > 1e-5, e.g. a deliberately lossy one) is
-    // applied as given.
+    // applied as given.  The double form applies the caller's double entries
+    // themselves (no rounding by the library), so it compensates nothing: a
+    // coin a few ulps from unitary is the caller's coin, not a rounding drift.
+    if (w->prec == QW_F64) fro = (double)d;
     const double alpha = std::sqrt(fro / d);
     w->coin_alpha = std::fabs(alpha - 1.0) <= 1e-5 ? alpha : 1.0;
     w->gain_fb = 1.0;
@@ -226,7 +244,7 @@ static void apply_global_coin(qw_walk *w, const double *h) {
         double mag[4], lam = 0.0;
         for (int i = 0; i < 4; ++i) { mag[i] = std::fabs(h[2 * i]); lam += mag[i] / 4; }
         bool eq = lam > 0.0;
-        for (int i = 0; i < 4; ++i) eq = eq && std::fabs(mag[i] - lam) <= 1e-14 * lam;
+        for (int i = 0; i < 4; ++i) eq = eq && std::fabs(mag[i] - lam) <= tol_rel * lam;
         if (eq) {
             const int m00 = h[0] > 0 ? 1 : -1, m01 = h[2] > 0 ? 1 : -1;
             const int m10 = h[4] > 0 ? 1 : -1, m11 = h[6] > 0 ? 1 : -1;

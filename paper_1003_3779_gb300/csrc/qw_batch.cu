@@ -48,6 +48,7 @@ struct WalkDesc {
     int64_t pitch;   // sites per plane, a multiple of 64
     int64_t poff;    // first index of the walk in the concatenated probabilities
     float c[8];      // coin, row-major complex (re, im)
+    float clo[8];    // QW_F32_COMP: the low parts, coin = c + clo to ~48 bits (else 0)
     // norm-drift compensation of the float-rounded coin (alpha = sqrt(|C_f|_F^2 / 2)):
     // the last round applies alpha^-T (g_last), the others g_main = 1; computed on
     // the host, so the kernel does no double arithmetic per round
@@ -68,10 +69,37 @@ struct BatchArgs {
     int K;           // steps per round once the light cone covers the cycle
     int Ks;          // steps per round while it does not (finer cone clipping)
     float cs[4];     // coin state at x0: (re, im) of coin 0 and coin 1
+    float cs_lo[4];  // QW_F32_COMP: their low parts
 };
 
 constexpr int BATCH_THREADS = 128;
 constexpr int BATCH_R = 16;
+// Sites per lane of the warp tiles: the double-float form holds four floats per
+// amplitude, so its tiles are half as long to stay in registers.
+constexpr int BATCH_R_COMP = 8;
+template <int P> constexpr int batch_r() { return P == P_COMP ? BATCH_R_COMP : BATCH_R; }
+
+// A compute real from the hi / lo floats the host split a double into.
+template <class R> __device__ __forceinline__ R real_hl(float hi, float lo);
+template <> __device__ __forceinline__ float real_hl<float>(float hi, float) { return hi; }
+template <> __device__ __forceinline__ ff real_hl<ff>(float hi, float lo) { return {hi, lo}; }
+
+// P(x) as the batch reports it (float) and its double contribution to the norm.
+// Float forms: the sum of squares in float, as the single walks' marginals;
+// the double-float form: in double from hi + lo, rounded once.
+template <int P>
+__device__ __forceinline__ float site_prob(View v, int64_t x, double &pd) {
+    using S = St<P>;
+    if constexpr (P == P_COMP) {
+        pd = norm2d(S::ld(v, 0, x)) + norm2d(S::ld(v, 1, x));
+        return (float)pd;
+    } else {
+        const Cx<float> u = S::ld(v, 0, x), w = S::ld(v, 1, x);
+        const float p = __fmaf_rn(u.re, u.re, __fmaf_rn(u.im, u.im, __fmaf_rn(w.re, w.re, w.im * w.im)));
+        pd = (double)p;
+        return p;
+    }
+}
 
 // Does the tile output range [a, b) meet the circular interval [x0 - r, x0 + r] (mod n)?
 __device__ __forceinline__ bool meets_cone(int64_t a, int64_t b, int64_t x0, int64_t r, int64_t n) {
@@ -222,7 +250,8 @@ template <int P, int CK>
 __global__ void __launch_bounds__(BATCH_THREADS)
 k_batch(BatchArgs a) {
     using S = St<P>;
-    constexpr int R = BATCH_R;
+    using real = typename S::real;
+    constexpr int R = batch_r<P>();
     constexpr int VEC = S::VEC;
     __shared__ int s_q;
     __shared__ double s_red[BATCH_THREADS / 32];
@@ -238,9 +267,9 @@ k_batch(BatchArgs a) {
         View in{static_cast<char *>(a.buf0) + d.base * S::SLOT_BYTES, d.pitch, 2};
         View out{static_cast<char *>(a.buf1) + d.base * S::SLOT_BYTES, d.pitch, 2};
 
-        // zero both buffers of this walk, then place the start
+        // zero both buffers of this walk (all plane slots), then place the start
         {
-            const int64_t nvec = 2 * d.pitch * S::SLOT_BYTES / 16;
+            const int64_t nvec = 2 * S::SLOTS_PER_COIN * d.pitch * S::SLOT_BYTES / 16;
             uint4 z = make_uint4(0, 0, 0, 0);
             for (int64_t i = threadIdx.x; i < nvec; i += blockDim.x) {
                 reinterpret_cast<uint4 *>(in.p)[i] = z;
@@ -249,14 +278,18 @@ k_batch(BatchArgs a) {
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            S::st(in, 0, d.x0, Cx<float>{a.cs[0], a.cs[1]});
-            S::st(in, 1, d.x0, Cx<float>{a.cs[2], a.cs[3]});
+            S::st(in, 0, d.x0, Cx<real>{real_hl<real>(a.cs[0], a.cs_lo[0]), real_hl<real>(a.cs[1], a.cs_lo[1])});
+            S::st(in, 1, d.x0, Cx<real>{real_hl<real>(a.cs[2], a.cs_lo[2]), real_hl<real>(a.cs[3], a.cs_lo[3])});
         }
         __syncthreads();
 
-        CoinP<float> cp;
+        CoinP<real> cp;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) { cp.re[e] = d.c[2 * e]; cp.im[e] = d.c[2 * e + 1]; }
+        for (int e = 0; e < 4; ++e) {
+            cp.re[e] = real_hl<real>(d.c[2 * e], d.clo[2 * e]);
+            cp.im[e] = real_hl<real>(d.c[2 * e + 1], d.clo[2 * e + 1]);
+        }
+        const real one = real_hl<real>(1.f, 0.f);
         int cur = 0;
         for (int64_t t0 = 0; t0 < d.T;) {
             // while the cone is narrower than the cycle, short rounds clip it more tightly
@@ -266,11 +299,11 @@ k_batch(BatchArgs a) {
             const int64_t ntiles = (d.n + W - 1) / W;
             const int64_t r = t0 + k;
             const bool all = 2 * r + 1 >= d.n;
-            const float g = (t0 + k >= d.T) ? d.g_last : d.g_main;
+            const real g = real_hl<real>((t0 + k >= d.T) ? d.g_last : d.g_main, 0.f);
             for (int64_t tile = wid; tile < ntiles; tile += nw) {
                 const int64_t o0 = tile * W, o1 = min(o0 + W, d.n);
                 if (!all && !meets_cone(o0, o1, d.x0, r, d.n)) continue;
-                tb_tile<P, R, CK, 0, 0>(in, out, d.n, k, W, tile, lane, cp, nullptr, 1.f, 1.f, g, g);
+                tb_tile<P, R, CK, 0, 0>(in, out, d.n, k, W, tile, lane, cp, nullptr, one, one, g, g);
             }
             __syncthreads();
             View t = in; in = out; out = t;
@@ -278,14 +311,13 @@ k_batch(BatchArgs a) {
             t0 += k;
         }
 
-        // marginals and norm of the final state
-        // P(x) is float output: the per-site sum of squares in float, the running norm in double
+        // marginals and norm of the final state: P(x) is float output, the
+        // running norm in double
         double acc = 0.0;
         for (int64_t x = threadIdx.x; x < d.n; x += blockDim.x) {
-            const Cx<float> u = S::ld(in, 0, x), v = S::ld(in, 1, x);
-            const float p = __fmaf_rn(u.re, u.re, __fmaf_rn(u.im, u.im, __fmaf_rn(v.re, v.re, v.im * v.im)));
-            a.P[d.poff + x] = p;
-            acc += (double)p;
+            double pd;
+            a.P[d.poff + x] = site_prob<P>(in, x, pd);
+            acc += pd;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -369,10 +401,9 @@ __device__ __forceinline__ void run_walk_sweep(const BatchArgs &a, int w, bool c
     }
     double acc = 0.0;
     for (int64_t x = g; x < d.n; x += gs) {
-        const Cx<float> u = S::ld(in, 0, x), v = S::ld(in, 1, x);
-        const float p = __fmaf_rn(u.re, u.re, __fmaf_rn(u.im, u.im, __fmaf_rn(v.re, v.re, v.im * v.im)));
-        a.P[d.poff + x] = p;
-        acc += (double)p;
+        double pd;
+        a.P[d.poff + x] = site_prob<P>(in, x, pd);
+        acc += pd;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -448,6 +479,7 @@ struct qw_batch {
     int variant = 1;                    // 0: warp tiles with halos, 1: light-cone window sweep
     int grid = 0, grid1 = 0;            // persistent grid of each variant (one wave)
     float cs[4] = {0, 0, 0, 0};
+    float cs_lo[4] = {0, 0, 0, 0};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool ran = false;
@@ -463,6 +495,14 @@ static qw_status batch_cuda(qw_batch *b, cudaError_t e, const char *where) {
     std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
     (void)cudaGetLastError();
     return batch_fail(b, e == cudaErrorMemoryAllocation ? QW_ENOMEM : QW_ECUDA, m);
+}
+
+static int batch_slot_bytes(int prec) { return prec == QW_F32_BF16STORE ? 4 : 8; }
+static int batch_slots(int prec) { return prec == QW_F32_COMP ? 4 : 2; }    // plane slots per walk
+static int batch_tile(int prec) { return prec == QW_F32_COMP ? BATCH_R_COMP : BATCH_R; }
+static int batch_kmax(int prec) { return 8 * batch_tile(prec); }
+static int batch_prec_code(int prec) {
+    return prec == QW_F32_BF16STORE ? P_BF16 : (prec == QW_F32_COMP ? P_COMP : P_F32);
 }
 
 // The window sweep's shared memory: a chunk buffer and the k-level edge
@@ -492,10 +532,14 @@ static cudaError_t batch_launch(qw_batch *b, cudaStream_t s) {
     a.buf0 = b->buf[0]; a.buf1 = b->buf[1]; a.P = b->P_dev; a.norms = b->norms_dev;
     a.counter = b->counter; a.final_buf = b->final_dev; a.K = b->K; a.Ks = b->K;
     std::memcpy(a.cs, b->cs, sizeof a.cs);
+    std::memcpy(a.cs_lo, b->cs_lo, sizeof a.cs_lo);
     a.nbig = b->nbig;
     cudaError_t e = cudaMemsetAsync(b->counter, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return e;
-    if (b->prec == QW_F32_BF16STORE) {
+    if (b->prec == QW_F32_COMP) {   // warp tiles only (no double-float sweep)
+        if (b->kind == CK_REAL) k_batch<P_COMP, CK_REAL><<<b->grid, BATCH_THREADS, 0, s>>>(a);
+        else k_batch<P_COMP, CK_COMPLEX><<<b->grid, BATCH_THREADS, 0, s>>>(a);
+    } else if (b->prec == QW_F32_BF16STORE) {
         if (b->kind == CK_REAL) e = launch_batch_kernel<P_BF16, CK_REAL>(b, a, s);
         else e = launch_batch_kernel<P_BF16, CK_COMPLEX>(b, a, s);
     } else {
@@ -551,7 +595,7 @@ qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T, const 
     if (!out) return QW_EINVAL;
     *out = nullptr;
     if (nwalks < 1 || !N || !T || !coins || !x0 || !coin_state) return QW_EINVAL;
-    if (prec != QW_F32 && prec != QW_F32_BF16STORE) return QW_EUNSUPPORTED;
+    if (prec != QW_F32 && prec != QW_F32_BF16STORE && prec != QW_F32_COMP) return QW_EUNSUPPORTED;
     for (int i = 0; i < nwalks; ++i)
         if (N[i] < 1 || N[i] > (int64_t(1) << 31) || T[i] < 0 || x0[i] < 0 || x0[i] >= N[i]) return QW_EINVAL;
 
@@ -560,7 +604,10 @@ qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T, const 
     b->nwalks = nwalks;
     b->prec = prec;
     b->stream = static_cast<cudaStream_t>(cuda_stream);
-    for (int i = 0; i < 4; ++i) b->cs[i] = (float)coin_state[i];
+    for (int i = 0; i < 4; ++i) {
+        b->cs[i] = (float)coin_state[i];
+        if (prec == QW_F32_COMP) b->cs_lo[i] = (float)(coin_state[i] - (double)b->cs[i]);
+    }
     b->walks.resize(nwalks);
     bool real = true;
     int64_t base = 0, poff = 0;
@@ -570,16 +617,18 @@ qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T, const 
         d.pitch = (N[i] + 63) / 64 * 64;
         d.base = base;
         d.poff = poff;
-        base += 2 * d.pitch;
+        base += batch_slots(prec) * d.pitch;
         poff += N[i];
         double fro = 0.0;
         for (int e = 0; e < 8; ++e) {
             d.c[e] = (float)coins[8 * i + e];
+            d.clo[e] = prec == QW_F32_COMP ? (float)(coins[8 * i + e] - (double)d.c[e]) : 0.f;
             fro += (double)d.c[e] * d.c[e];
             if (e % 2 == 1 && coins[8 * i + e] != 0.0) real = false;
         }
         const double alpha = std::sqrt(fro / 2.0);
-        d.alpha = std::fabs(alpha - 1.0) <= 1e-5 ? alpha : 1.0;
+        // hi + lo carries the coin to ~48 bits: no norm drift to compensate
+        d.alpha = (prec != QW_F32_COMP && std::fabs(alpha - 1.0) <= 1e-5) ? alpha : 1.0;
     }
     b->kind = real ? CK_REAL : CK_COMPLEX;
     b->total_slots = base;
@@ -595,8 +644,7 @@ qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T, const 
         b->work[i] = tc * tc + (t - tc) * n;
     }
     std::stable_sort(b->order.begin(), b->order.end(), [&](int p, int q) { return b->work[p] > b->work[q]; });
-    const int slot = prec == QW_F32_BF16STORE ? 4 : 8;
-    b->buf_bytes = (size_t)base * slot;
+    b->buf_bytes = (size_t)base * batch_slot_bytes(prec);
 
     cudaError_t e = cudaSuccess;
     int dev = 0, sms = 0, per_sm = 0;
@@ -604,10 +652,12 @@ qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T, const 
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, prec == QW_F32_BF16STORE ? (const void *)k_batch<P_BF16, CK_REAL> : (const void *)k_batch<P_F32, CK_REAL>,
+            &per_sm, prec == QW_F32_BF16STORE ? (const void *)k_batch<P_BF16, CK_REAL>
+                     : prec == QW_F32_COMP    ? (const void *)k_batch<P_COMP, CK_REAL>
+                                              : (const void *)k_batch<P_F32, CK_REAL>,
             BATCH_THREADS, 0);
     int per_sm1 = 0;
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && prec != QW_F32_COMP) {
         // the window sweep at the largest k it is planned with (the occupancy of smaller k is no lower)
         const size_t smem = batch_smem(prec, 1, 8 * BATCH_R);
         const void *f1 = prec == QW_F32_BF16STORE ? (const void *)k_batch_sweep<P_BF16, CK_REAL> : (const void *)k_batch_sweep<P_F32, CK_REAL>;
@@ -635,6 +685,7 @@ qw_status qw_batch_create(int nwalks, const int64_t *N, const int64_t *T, const 
     b->grid = std::max(1, std::min(nwalks, sms * std::max(1, per_sm)));
     b->grid1 = std::max(1, std::min(nwalks, sms * std::max(1, per_sm1)));
     b->nbig = nwalks / 16;   // the largest sixteenth on CTAs (the autotuner refines it)
+    if (prec == QW_F32_COMP) { b->variant = 0; b->K = 32; }
     *out = b;
     return QW_OK;
 }
@@ -661,8 +712,8 @@ qw_status qw_batch_step(qw_batch *b) {
 
 qw_status qw_batch_set_plan(qw_batch *b, int depth_k) {
     if (!b) return QW_EINVAL;
-    if (depth_k < 1 || depth_k > 8 * BATCH_R)
-        return batch_fail(b, QW_EINVAL, "k must be in [1, " + std::to_string(8 * BATCH_R) + "]");
+    if (depth_k < 1 || depth_k > batch_kmax(b->prec))
+        return batch_fail(b, QW_EINVAL, "k must be in [1, " + std::to_string(batch_kmax(b->prec)) + "]");
     if (depth_k != b->K) {
         cudaStreamSynchronize(b->stream);
         drop_graph(b);   // the captured launch carries k
@@ -677,13 +728,15 @@ qw_status qw_batch_set_plan(qw_batch *b, int depth_k) {
 qw_status qw_batch_get_plan(const qw_batch *b, int *depth_k, int *tile) {
     if (!b || !depth_k || !tile) return QW_EINVAL;
     *depth_k = b->K;
-    *tile = BATCH_R;
+    *tile = batch_tile(b->prec);
     return QW_OK;
 }
 
 qw_status qw_batch_set_plan_ex(qw_batch *b, int depth_k, int variant) {
     if (!b) return QW_EINVAL;
     if (variant != 0 && variant != 1) return batch_fail(b, QW_EINVAL, "variant must be 0 (tiles) or 1 (window sweep)");
+    if (variant == 1 && b->prec == QW_F32_COMP)
+        return batch_fail(b, QW_EUNSUPPORTED, "the double-float batch runs the warp tiles (variant 0) only");
     qw_status st = qw_batch_set_plan(b, depth_k);
     if (st != QW_OK) return st;
     if (variant != b->variant) {
@@ -711,7 +764,7 @@ int qw_batch_cta_walks(const qw_batch *b) { return b ? b->nbig : -1; }
 qw_status qw_batch_get_plan_ex(const qw_batch *b, int *depth_k, int *tile, int *variant) {
     if (!b || !depth_k || !tile || !variant) return QW_EINVAL;
     *depth_k = b->K;
-    *tile = BATCH_R;
+    *tile = batch_tile(b->prec);
     *variant = b->variant;
     return QW_OK;
 }
@@ -738,7 +791,7 @@ qw_status qw_batch_autotune(qw_batch *b, char *report, size_t report_len) {
     };
     // variant 0 over k
     for (int k : ks) {
-        if (k > 8 * BATCH_R) break;
+        if (k > batch_kmax(b->prec)) break;
         float ms = 0.f;
         if (qw_batch_set_plan_ex(b, k, 0) != QW_OK) { e = cudaErrorUnknown; break; }
         if (!time_plan(ms)) break;
@@ -748,7 +801,7 @@ qw_status qw_batch_autotune(qw_batch *b, char *report, size_t report_len) {
     // warps), at k = 96, then k at that split
     int n1 = b->nbig;
     float best1 = 1e30f;
-    if (e == cudaSuccess && qw_batch_set_plan_ex(b, std::min(96, 8 * BATCH_R), 1) == QW_OK) {
+    if (e == cudaSuccess && b->prec != QW_F32_COMP && qw_batch_set_plan_ex(b, std::min(96, 8 * BATCH_R), 1) == QW_OK) {
         for (int n : {0, 16, 32, 64, 128, 256, 512, 1024, b->nwalks}) {
             if (n > b->nwalks) continue;
             qw_batch_set_cta_walks(b, n);
@@ -759,7 +812,7 @@ qw_status qw_batch_autotune(qw_batch *b, char *report, size_t report_len) {
         qw_batch_set_cta_walks(b, n1);
     }
     for (int k : ks) {
-        if (e != cudaSuccess || k > 8 * BATCH_R) break;
+        if (e != cudaSuccess || b->prec == QW_F32_COMP || k > 8 * BATCH_R) break;
         float ms = 0.f;
         if (qw_batch_set_plan_ex(b, k, 1) != QW_OK) { e = cudaErrorUnknown; break; }
         if (!time_plan(ms)) break;
@@ -773,7 +826,7 @@ qw_status qw_batch_autotune(qw_batch *b, char *report, size_t report_len) {
     if (report && report_len) {
         std::snprintf(report, report_len,
                       "{\"tuned\": true, \"k\": %d, \"tile\": %d, \"variant\": \"%s\", \"cta_walks\": %d, "
-                      "\"ms\": %.6g}", best_k, BATCH_R, best_v ? "window_sweep" : "tiles", best_v ? b->nbig : b->nwalks, best);
+                      "\"ms\": %.6g}", best_k, batch_tile(b->prec), best_v ? "window_sweep" : "tiles", best_v ? b->nbig : b->nwalks, best);
     }
     return QW_OK;
 }
@@ -801,13 +854,12 @@ qw_status qw_batch_get_state(qw_batch *b, int walk, void *amp_out, qw_cdtype dty
     cudaError_t e = cudaMemcpyAsync(&which, b->final_dev + walk, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return batch_cuda(b, e, "batch state");
-    const int slot = b->prec == QW_F32_BF16STORE ? 4 : 8;
-    View v{static_cast<char *>(b->buf[which]) + d.base * slot, d.pitch, 2};
+    View v{static_cast<char *>(b->buf[which]) + d.base * batch_slot_bytes(b->prec), d.pitch, 2};
     const size_t eb = dtype == QW_C128 ? 16 : 8;
     void *tmp = nullptr;
     e = dev_alloc(&tmp, 2 * (size_t)d.n * eb);
     if (e != cudaSuccess) return batch_cuda(b, e, "batch state staging");
-    const int prec = b->prec == QW_F32_BF16STORE ? P_BF16 : P_F32;
+    const int prec = batch_prec_code(b->prec);
     for (int c = 0; c < 2 && e == cudaSuccess; ++c)
         e = launch_export(prec, v, d.n, static_cast<char *>(tmp) + c * d.n * eb, dtype == QW_C64, 0, d.n, c, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(amp_out, tmp, 2 * (size_t)d.n * eb, cudaMemcpyDeviceToHost, b->stream);

@@ -12,9 +12,10 @@
 // the process exits.
 //
 // The arithmetic is that of qw_probabilities: P(v) = sum_c |psi(v,c)|^2 per site,
-// and the norm as the fixed-order sum of per-block double partials (one block
-// per QW_NOALLOC_SITES_PER_BLOCK sites, then one warp adds the partials in block
-// order), so a given size always sums in the same order.
+// and the norm as a fixed-order sum of double partials.  The grid has
+// ceil(nsites / NA_SITES_PER_BLOCK) blocks; each sums a strided set of sites
+// (grid-stride loop) into one partial, then one warp adds the partials in
+// block order.  The grid, and so the summation order, depends only on nsites.
 #include <mutex>
 
 #include "qw_internal.cuh"
@@ -85,7 +86,11 @@ __global__ void k_sum_partials_noalloc(const double *partials, int n, double *ou
 
 // Device address of the scratch array on the current device.  The array's
 // name is only a host-side stand-in in host code, so the address is looked up
-// once per device with that device current.
+// once per device with that device current.  The same first call loads all
+// three kernels of this file on the device (cudaFuncGetAttributes), so that a
+// later call, with either P type, loads no module code.  The address is kept
+// for the life of the process: after a cudaDeviceReset of that device, which
+// invalidates every other handle of the library as well, it is stale.
 cudaError_t scratch_for_current_device(double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -95,6 +100,11 @@ cudaError_t scratch_for_current_device(double **out) {
     if (!g_na_ptr[dev]) {
         double *p = nullptr;
         e = cudaGetSymbolAddress((void **)&p, g_noalloc_partials);
+        if (e != cudaSuccess) return e;
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, k_marginals_noalloc<0>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_marginals_noalloc<1>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_sum_partials_noalloc);
         if (e != cudaSuccess) return e;
         g_na_ptr[dev] = p;
     }

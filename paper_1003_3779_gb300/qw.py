@@ -288,12 +288,36 @@ def qw_backward(h, rect, T, K, grad_out):
 
 def qw_probabilities_noalloc(amp, P_out=None, norm_out=None, stream=None):
     """Marginals and norm of a caller-owned device state without any library
-    allocation (see include/qw.h).  amp: torch complex64/complex128 tensor of
-    shape (d, ...) on the GPU; P_out: float32/float64 device tensor or None;
-    norm_out: one-element float64 device tensor or None.  Returns the status."""
+    allocation (see include/qw.h).  amp: contiguous torch complex64/complex128
+    tensor of shape (d, ...) on the GPU, d = 2 or 4; P_out: contiguous
+    float32/float64 tensor with at least one element per site, or None;
+    norm_out: float64 tensor with at least one element, or None.  All on the
+    same GPU.  Returns the status.  Raises ValueError on any other argument:
+    the library reads and writes these pointers as device memory of exactly
+    those types and sizes, so a host tensor, a strided view or a short output
+    would be an out-of-bounds access on the GPU."""
     import torch
+    if not isinstance(amp, torch.Tensor) or not amp.is_cuda:
+        raise ValueError("amp must be a CUDA tensor")
+    if amp.dtype not in (torch.complex64, torch.complex128):
+        raise ValueError(f"amp must be complex64 or complex128, not {amp.dtype}")
+    if not amp.is_contiguous() or amp.dim() < 2:
+        raise ValueError("amp must be a contiguous tensor of shape (d, sites...)")
     d = int(amp.shape[0])
     ns = int(amp[0].numel())
+    dev = amp.device
+    if P_out is not None:
+        if not isinstance(P_out, torch.Tensor) or not P_out.is_cuda or P_out.device != dev:
+            raise ValueError("P_out must be a CUDA tensor on the device of amp")
+        if P_out.dtype not in (torch.float32, torch.float64):
+            raise ValueError(f"P_out must be float32 or float64, not {P_out.dtype}")
+        if not P_out.is_contiguous() or P_out.numel() < ns:
+            raise ValueError(f"P_out must be contiguous with at least {ns} elements")
+    if norm_out is not None:
+        if not isinstance(norm_out, torch.Tensor) or not norm_out.is_cuda or norm_out.device != dev:
+            raise ValueError("norm_out must be a CUDA tensor on the device of amp")
+        if norm_out.dtype != torch.float64 or norm_out.numel() < 1:
+            raise ValueError("norm_out must be a float64 tensor with at least one element")
     dt = C64 if amp.dtype == torch.complex64 else C128
     pd = R32 if (P_out is not None and P_out.dtype == torch.float32) else R64
     return lib().qw_probabilities_noalloc(_ptr(amp), dt, d, ns, _ptr(P_out), pd, _ptr(norm_out),
@@ -429,7 +453,8 @@ class Batch:
     """Many independent walks on cycles, advanced in one persistent launch.
 
     N, T, x0: integer arrays (one entry per walk); coins: (nwalks, 2, 2)
-    complex; coin_state: the two coin amplitudes at x0; prec "f32" or "bf16".
+    complex; coin_state: the two coin amplitudes at x0; prec "f32", "bf16" or
+    "comp" (double-float).
     """
 
     def __init__(self, N, T, coins, x0, coin_state=(2 ** -0.5, 1j * 2 ** -0.5), prec="f32",

@@ -26,15 +26,24 @@ def qw():
     return qw
 
 
-def test_cycle_2e27_T4096_sweep_sampled(qw):
-    """N = 2^27, SU(2) theta = pi/4, T = 4096, FP32, the random complex64 state of
-    the benchmark, swept at k = 384 with 32 sites per lane (as the benchmark's
-    autotuner picks): eight sampled sites against the oracle, plus the norm."""
+# the benchmark's coin classes: SU(2) theta = pi/4 (the Hadamard class, four
+# additions per site-step), a real rotation theta = 0.3 and a complex SU(2) coin
+FULL_COINS = {"hadamard_class": inputs.su2(np.pi / 4), "real": inputs.su2(0.3),
+              "complex": inputs.su2(np.pi / 4, 0.3, -0.2)}
+
+
+@pytest.mark.parametrize("coin", list(FULL_COINS))
+def test_cycle_2e27_T4096_sweep_sampled(qw, coin):
+    """N = 2^27, T = 4096, FP32, the random complex64 state of the benchmark,
+    swept at k = 384 with 32 sites per lane (as the benchmark's autotuner picks
+    for the headline coin): eight sampled sites against the oracle, plus the
+    norm, for each coin class the benchmark times."""
     import torch
     N, T = 1 << 27, 4096
-    C = inputs.su2(np.pi / 4)
+    C = FULL_COINS[coin]
     psi0 = inputs.random_state((2, N), seed=1, dtype=np.complex64)
     w = qw.Walk((N,), prec="f32").set_coin(C).set_plan_ex(384, 32, 1)
+    assert w.describe()["coin_kind"] == coin
     w.set_state(torch.from_numpy(psi0).cuda())
     w.step(T)
     assert abs(w.norm() - 1) < T * 4 * U32

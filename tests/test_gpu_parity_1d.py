@@ -325,3 +325,32 @@ def test_sweep_rejected_where_it_cannot_run(qw):
     with pytest.raises(qw.QWError):
         w.set_plan_ex(16, 0, 1)          # no sweep kernel for the double-float form
     w.close()
+
+
+@pytest.mark.parametrize("prec", ["f64"])
+def test_near_hadamard_coin_runs_as_given_in_double(qw, prec):
+    """A coin a few double ulps away from 1/sqrt2 * [[1, 1], [1, -1]] is applied
+    as given in the double form (not replaced by the exact Hadamard-class
+    kernel): at T = 4096 the result follows the oracle of the
+    perturbed coin, whose distance to the unperturbed walk is far above the
+    rounding error."""
+    N, T = 2048, 4096
+    C = inputs.hadamard().copy()
+    C[0, 0] += 5e-15
+    psi0 = inputs.random_state((2, N), seed=61)
+    want = oracle.evolve(psi0, C, T)
+    exact = oracle.evolve(psi0, inputs.hadamard(), T)
+    gap = maxabs(want, exact)
+    w = qw.Walk((N,), prec=prec).set_coin(C)
+    assert w.describe()["coin_kind"] == "real"
+    w.set_state(psi0).step(T)
+    got = w.state()
+    P, _ = w.probabilities()
+    w.close()
+    assert maxabs(got, want) < gap / 8, (maxabs(got, want), gap)
+    if prec == "f64":
+        assert l1(P, oracle.probabilities(want)[0]) < 1e-12
+    # the exact coin still takes the addition-only kernel
+    w = qw.Walk((N,), prec=prec).set_coin(inputs.hadamard())
+    assert w.describe()["coin_kind"] == "hadamard_class"
+    w.close()

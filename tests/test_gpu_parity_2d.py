@@ -292,3 +292,32 @@ def test_tiled_generic_step_cycle(qw, prec, bc, shift, N):
     w.step(T)
     assert maxabs(w.state(), want) < amp_tol(prec, T)
     w.close()
+
+
+@pytest.mark.parametrize("prec", ["f64"])
+@pytest.mark.parametrize("name", ["grover", "hadamard2"])
+def test_near_grover_and_hh_coins_run_as_given_in_double(qw, prec, name):
+    """A Grover or H (x) H coin scaled by 1 + 1.8e-15 (every entry moved by
+    about 8 ulps, within 1e-15) is applied as given in the double form: after
+    T = 1024 steps the state follows the oracle of the scaled coin, far closer
+    than the scaling moved it.  The unscaled coin, H (x) H built as
+    kron(H, H) of the rounded 1/sqrt2 included, keeps its own kernel."""
+    L, T = 32, 1024
+    base = inputs.grover() if name == "grover" else inputs.hadamard2()
+    C = base * (1 + 1.8e-15)
+    psi0 = inputs.random_state((4, L, L), seed=62)
+    want = oracle.evolve(psi0, C, T)
+    exact = oracle.evolve(psi0, base, T)
+    gap = maxabs(want, exact)
+    w = qw.Walk((L, L), prec=prec).set_coin(C)
+    assert w.describe()["coin_kind"] == "real"
+    w.set_state(psi0).step(T)
+    got = w.state()
+    P, _ = w.probabilities()
+    w.close()
+    assert maxabs(got, want) < gap / 8, (maxabs(got, want), gap)
+    if prec == "f64":
+        assert l1(P, oracle.probabilities(want)[0]) < 1e-12
+    w = qw.Walk((L, L), prec=prec).set_coin(base)
+    assert w.describe()["coin_kind"] == name
+    w.close()
