@@ -549,7 +549,7 @@ def run_gpu(args, rank, world, local):
         z = torch.randn((4, L, L), dtype=torch.complex64, device=f"cuda:{local}", generator=g)
         z /= z.abs().pow(2).sum().sqrt()
         for name, coin, shift in (("grover_moving", _in.grover(), 0), ("hh_moving", _in.hadamard2(), 0),
-                                  ("grover_flipflop", _in.grover(), 1)):
+                                  ("grover_flipflop", _in.grover(), 1), ("diagonal_hh", _in.hadamard2(), 2)):
             w2 = qw.Walk((L, L), prec="f32", shift=shift).set_coin(coin).set_state(z)
             for kk in (1, 8):
                 w2.set_plan(kk)
@@ -567,13 +567,12 @@ def run_gpu(args, rank, world, local):
                                           "frac_of_measured": gbs / hbm_gbs, "frac_of_8000": gbs / 8000.0}
             w2.close()
         # the rows beyond the periodic lattice walk, same lattice and state: the
-        # diagonal lattice (fused step), and the generic kernel with a segment
-        # boundary and 5 % of the links closed (fixed mask, 2 more bytes per
-        # site-step), or with links closed at random afresh at every step
-        # (p = 0.05, Philox in the kernel, no mask traffic)
+        # generic kernel with a segment boundary and 5 % of the links closed
+        # (fixed mask, 2 more bytes per site-step), or with links closed at
+        # random afresh at every step (p = 0.05, Philox in the kernel, no mask
+        # traffic); the diagonal lattice is timed above with the axis lattice
         mask = (torch.rand((2, L * L), generator=torch.Generator().manual_seed(3)) < 0.05).to(torch.uint8).cuda()
         for name, kw, setup, nbytes in (
-                ("diagonal_hh", dict(shift=qw.SHIFT_DIAGONAL), lambda w_: w_.set_coin(_in.hadamard2()), 64.0),
                 ("segment_fixed_links_5pct", dict(bc=qw.BC_SEGMENT),
                  lambda w_: w_.set_coin(_in.grover()).set_links(mask), 66.0),
                 ("random_links_5pct_per_step", dict(),
@@ -817,12 +816,37 @@ def run_case(args):
         w.close()
         print(json.dumps(out))
         return
-    if args.case == "torus":
+    if args.case == "cycle":
+        # the 1D walk on a cycle of --n-sites sites (default 2^24), FP32, a random
+        # state, --coin class, --plan "k,tile,variant" (default: autotuned);
+        # 4 launches after two warm-up launches
+        n = args.n_sites if args.n_sites != N_SITES else 1 << 24
+        C = {"hadamard_class": _in.su2(THETA), "real": _in.su2(0.3),
+             "complex": _in.su2(THETA, 0.3, -0.2)}[args.coin]
+        z = torch.from_numpy(_in.random_state((2, n), seed=SEED, dtype=np.complex64)).cuda()
+        w = qw.Walk((n,), prec="f32").set_coin(C).set_state(z)
+        if args.plan:
+            f = [int(x) for x in args.plan.split(",")]
+            w.set_plan_ex(f[0], f[1], f[2] if len(f) > 2 else 1)
+        else:
+            out["autotune"] = json.loads(w.autotune())
+        k = w.plan_ex()[0]
+        w.step(2 * k)
+        a, b = ev(), ev()
+        a.record(stream)
+        w.step(4 * k)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out.update(n=n, coin=args.coin, plan=list(w.plan_ex()), kernel=w.describe()["path"],
+                   ms_per_step=a.elapsed_time(b) / (4 * k), norm=w.norm())
+        w.close()
+    elif args.case == "torus":
         L = args.n_sites
         g = torch.Generator(device="cuda").manual_seed(2)
         z = torch.randn((4, L, L), dtype=torch.complex64, device="cuda", generator=g)
         z /= z.abs().pow(2).sum().sqrt()
-        w = qw.Walk((L, L), prec="f32").set_coin(_in.grover()).set_state(z)
+        coin2 = _in.hadamard2() if args.shift == 2 else _in.grover()
+        w = qw.Walk((L, L), prec="f32", shift=args.shift).set_coin(coin2).set_state(z)
         k = int(args.plan.split(",")[0]) if args.plan else 8
         w.set_plan(k)
         w.step(2 * k)
@@ -831,7 +855,7 @@ def run_case(args):
         w.step(8 * k)
         b.record(stream)
         torch.cuda.synchronize()
-        out.update(L=L, k=k, kernel=w.describe()["path"], ms_per_step=a.elapsed_time(b) / (8 * k))
+        out.update(L=L, k=k, shift=args.shift, kernel=w.describe()["path"], ms_per_step=a.elapsed_time(b) / (8 * k))
         w.close()
     elif args.case == "batch":
         N, T, th, x0 = _in.batch_1d_params(nwalks=args.walks)
@@ -871,7 +895,11 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--n-sites", type=int, default=N_SITES,
                     help="cycle length (default 2^27; smaller only for profiling captures)")
-    ap.add_argument("--case", default="", choices=["", "torus", "batch", "grad", "graph", "generic"],
+    ap.add_argument("--shift", type=int, default=0, choices=[0, 1, 2],
+                    help="shift of the torus case (2: diagonal lattice, H (x) H; else Grover)")
+    ap.add_argument("--coin", default="hadamard_class", choices=["hadamard_class", "real", "complex"],
+                    help="coin class of the cycle case")
+    ap.add_argument("--case", default="", choices=["", "cycle", "torus", "batch", "grad", "graph", "generic"],
                     help="run a small named workload for kernel captures instead of the benchmark")
     ap.add_argument("--walks", type=int, default=4096, help="walks of the batch case")
     ap.add_argument("--plan", default="",

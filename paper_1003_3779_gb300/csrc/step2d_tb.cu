@@ -6,42 +6,70 @@
 
 namespace qw {
 
-template <int KT, int CK, int FF>
+template <int KT, int CK, int SH>
 static cudaError_t go2d_tb(const Step2DArgs &a, const CoinP<float> &cp, cudaStream_t s) {
     constexpr int R = 2;
     const int64_t W = 32 * R - 2 * KT;                 // output columns per strip
     const int64_t nstrips = (a.nx + W - 1) / W;
-    // rows per warp: enough warps for about three waves of resident warps,
-    // and at least 8 KT rows so the 2 KT rows of warm-up stay small
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t target = (int64_t)sms * 16 * 3;
-    const int64_t want_chunks = std::max<int64_t>(1, (target + nstrips - 1) / nstrips);
-    int64_t H = std::max<int64_t>(8 * KT, (a.ny + want_chunks - 1) / want_chunks);
+    constexpr size_t smem = step2d_tb_smem<KT, SH>();
+    auto kern = k_step2d_tb<P_F32, KT, CK, SH>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // Rows per warp.  Every warp of a launch does about the same work, so the
+    // launch takes ceil(warps / resident warps) waves of (H + 2 KT) rows each;
+    // pick the row chunk H (at least 8 KT rows, so the 2 KT rows of warm-up
+    // stay small) that minimises that product: no last wave that runs nearly
+    // empty.
+    // resident warps of this instance (looked up once; every device here is the same part)
+    static int64_t resident = 0;
+    if (!resident) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        resident = (int64_t)sms * per_sm * 4;
+    }
+    int64_t H = std::min<int64_t>(a.ny, 8 * KT), best = -1;
+    for (int64_t nc = 1; nc <= (a.ny + 8 * KT - 1) / (8 * KT); ++nc) {
+        const int64_t h = (a.ny + nc - 1) / nc;
+        if (h < 8 * KT && nc > 1) break;
+        const int64_t waves = (nstrips * nc + resident - 1) / resident;
+        const int64_t cost = waves * (h + 2 * KT);
+        if (best < 0 || cost < best) { best = cost; H = h; }
+    }
     H = std::min<int64_t>(H, a.ny);
     const int64_t nchunks = (a.ny + H - 1) / H;
     const int64_t nwarps = nstrips * nchunks;
     const int64_t blocks = (nwarps + 3) / 4;
-    k_step2d_tb<P_F32, KT, CK, FF><<<(unsigned)blocks, 128, step2d_tb_smem(), s>>>(a.in, a.out, a.nx, a.ny, W, nstrips,
-                                                                                 H, nchunks, cp, (float)a.gain);
+    kern<<<(unsigned)blocks, 128, smem, s>>>(a.in, a.out, a.nx, a.ny, W, nstrips, H, nchunks, cp, (float)a.gain);
     return cudaGetLastError();
+}
+
+template <int KT, int CK>
+static cudaError_t go2d_tb_shift(const Step2DArgs &a, const CoinP<float> &cp, cudaStream_t s) {
+    switch (a.shift) {
+        case QW_SHIFT_MOVING: return go2d_tb<KT, CK, QW_SHIFT_MOVING>(a, cp, s);
+        case QW_SHIFT_FLIPFLOP: return go2d_tb<KT, CK, QW_SHIFT_FLIPFLOP>(a, cp, s);
+        case QW_SHIFT_DIAGONAL: return go2d_tb<KT, CK, QW_SHIFT_DIAGONAL>(a, cp, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <int KT>
 static cudaError_t go2d_tb_kind(const Step2DArgs &a, const CoinP<float> &cp, cudaStream_t s) {
-    const bool ff = a.shift == QW_SHIFT_FLIPFLOP;
     switch (a.kind) {
-        case CK_REAL: return ff ? go2d_tb<KT, CK_REAL, 1>(a, cp, s) : go2d_tb<KT, CK_REAL, 0>(a, cp, s);
-        case CK_COMPLEX: return ff ? go2d_tb<KT, CK_COMPLEX, 1>(a, cp, s) : go2d_tb<KT, CK_COMPLEX, 0>(a, cp, s);
-        case CK_GROVER: return ff ? go2d_tb<KT, CK_GROVER, 1>(a, cp, s) : go2d_tb<KT, CK_GROVER, 0>(a, cp, s);
-        case CK_HH: return ff ? go2d_tb<KT, CK_HH, 1>(a, cp, s) : go2d_tb<KT, CK_HH, 0>(a, cp, s);
+        case CK_REAL: return go2d_tb_shift<KT, CK_REAL>(a, cp, s);
+        case CK_COMPLEX: return go2d_tb_shift<KT, CK_COMPLEX>(a, cp, s);
+        case CK_GROVER: return go2d_tb_shift<KT, CK_GROVER>(a, cp, s);
+        case CK_HH: return go2d_tb_shift<KT, CK_HH>(a, cp, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 bool step2d_tb_ok(int prec, int kind, int K, int shift) {
-    return prec == QW_F32 && (K == 4 || K == 8) && shift != QW_SHIFT_DIAGONAL &&
+    return prec == QW_F32 && (K == 4 || K == 8) &&
+           (shift == QW_SHIFT_MOVING || shift == QW_SHIFT_FLIPFLOP || shift == QW_SHIFT_DIAGONAL) &&
            (kind == CK_REAL || kind == CK_COMPLEX || kind == CK_GROVER || kind == CK_HH);
 }
 

@@ -60,11 +60,14 @@ def test_cycle_2e27_T4096_sweep_sampled(qw, coin):
     w.close()
 
 
-@pytest.mark.parametrize("coin,shift", [("grover", 0), ("hh", 0), ("grover", 1)])
+@pytest.mark.parametrize("coin,shift", [("grover", 0), ("hh", 0), ("grover", 1), ("hh", 2)])
 def test_torus_8192_streaming_sampled(qw, coin, shift):
     """8192 x 8192 torus, FP32, the streaming kernel at k = 8 as the benchmark
     times it, T = 64 (eight launches), a random state: sampled sites (corners,
-    edges, interior) against the oracle on their (2T + 1)^2 windows."""
+    edges, interior) against the oracle on their (2T + 1)^2 windows (an
+    absorbing edge on the axis lattice; on the diagonal lattice, where the
+    oracle takes only the periodic edge, the window as a torus of its own: a
+    path of T steps to the centre starts within T of it and wraps nowhere)."""
     import torch
     L, T = 8192, 64
     C = {"grover": inputs.grover(), "hh": inputs.hadamard2()}[coin]
@@ -81,7 +84,8 @@ def test_torus_8192_streaming_sampled(qw, coin, shift):
         ix = (x - T + np.arange(M)) % L
         iy = (y - T + np.arange(M)) % L
         win = psi0[:, iy][:, :, ix].astype(np.complex128)
-        want = oracle.evolve(win, C, T, shift=shift, bc=oracle.BC_LINE)[:, T, T]
+        bc = oracle.BC_PERIODIC if shift == 2 else oracle.BC_LINE
+        want = oracle.evolve(win, C, T, shift=shift, bc=bc)[:, T, T]
         scale = float(np.sqrt((np.abs(win) ** 2).sum()))
         err = float(np.abs(got[:, y, x].astype(np.complex128) - want).max())
         assert err <= T * 4 * U32 * scale, (x, y, err, scale)

@@ -155,11 +155,12 @@ def test_tiny_torus(qw, L):
 
 @pytest.mark.parametrize("k", [4, 8])
 @pytest.mark.parametrize("coin", ["grover", "hh", "real", "complex"])
-@pytest.mark.parametrize("shift", [0, 1])
+@pytest.mark.parametrize("shift", [0, 1, 2])
 @pytest.mark.parametrize("dims", [(200, 37), (64, 300), (48, 9)])
 def test_torus_temporal_blocking(qw, k, coin, shift, dims):
     """The streaming kernel (k steps per HBM round trip) against the oracle:
-    strips and row chunks with ragged ends, wrap in x and y, T not a multiple of k."""
+    strips and row chunks with ragged ends, wrap in x and y, T not a multiple
+    of k; moving, flip-flop and diagonal-lattice shifts."""
     rng = np.random.default_rng(["grover", "hh", "real", "complex"].index(coin) + 10 * k)
     C = coin_named(coin, rng)
     Lx, Ly = dims
@@ -167,6 +168,7 @@ def test_torus_temporal_blocking(qw, k, coin, shift, dims):
     psi0 = inputs.random_state((4, Ly, Lx), seed=26)
     want = oracle.evolve(psi0, C, T, shift=shift)
     w = qw.Walk((Lx, Ly), prec="f32", shift=shift).set_coin(C).set_plan(k)
+    assert w.describe()["path"] == "k_step2d_tb"
     w.set_state(psi0)
     w.step(T)
     assert maxabs(w.state(), want) < amp_tol("f32", T)
