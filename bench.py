@@ -369,6 +369,52 @@ def coin_class_leg(qw, C, dev0, stream, sm_max_mhz, hbm_gbs):
                                       "frac": 32.0 * N_SITES * launches / t / 1e9 / hbm_gbs}}}
 
 
+def localized_legs(qw, stream):
+    """Walks from one site: the diagonal lattice (H (x) H) on the 8192^2 torus
+    from its centre for T = 500, and the SU(2) theta = pi/4 line on the cycle of
+    2^27 sites from its centre for T = 4096, FP32, default plans.  Each is timed
+    with light-cone clipping and with it off (the whole lattice every step);
+    dense rates count every site of the lattice, active ones the light cone."""
+    import torch
+    from paper_1003_3779_gb300 import inputs as _in
+    out = {}
+    cases = (
+        ("diagonal_hh_8192_from_centre_T500", (8192, 8192), 500, qw.SHIFT_DIAGONAL, _in.hadamard2()),
+        ("line_su2_2e27_from_centre_T4096", (N_SITES,), T_STEPS, qw.SHIFT_MOVING, _in.su2(THETA)),
+    )
+    for name, dims, T, shift, C in cases:
+        d = 2 * len(dims)
+        z = torch.zeros((d,) + tuple(reversed(dims)), dtype=torch.complex64, device="cuda")
+        centre = tuple(n // 2 for n in reversed(dims))
+        for c in range(d):
+            z[(c,) + centre] = 0.5 if d == 4 else (2 ** -0.5 if c == 0 else 1j * 2 ** -0.5)
+        nsites = int(np.prod(dims))
+        cone = sum(min((2 * t + 1) ** len(dims), nsites) for t in range(1, T + 1))   # light-cone site-steps
+        leg = {"sites": nsites, "T": T, "active_site_steps": float(cone)}
+        for clip in (True, False):
+            w = qw.Walk(dims, prec="f32", shift=shift).set_coin(C).set_clipping(clip)
+            w.set_state(z)
+            w.step(16)                       # warm-up (kernels loaded, plans fixed)
+            w.set_state(z)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            w.step(T)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / 1e3
+            desc = w.describe()
+            leg["clipped" if clip else "whole_lattice"] = {
+                "ms": t * 1e3, "dense_site_coin_updates_per_s": d * nsites * T / t,
+                "active_site_coin_updates_per_s": d * cone / t, "kernel": desc["path"], "k": desc["k"],
+                "support_after": desc["support"], "norm": w.norm()}
+            w.close()
+        leg["clipping_speedup"] = leg["whole_lattice"]["ms"] / leg["clipped"]["ms"]
+        out[name] = leg
+        del z
+    return out
+
+
 def run_gpu(args, rank, world, local):
     import torch
     import paper_1003_3779_gb300.qw as qw
@@ -609,6 +655,13 @@ def run_gpu(args, rank, world, local):
             "frac_of_measured": 32.0 * N_SITES / ts / 1e9 / hbm_gbs, "norm": ws.norm()}
         ws.close()
 
+    # the paper's own timed shapes: a walker started on one site (the line walk of
+    # Sec. 3 and the 2D walk of Tables 2-3 on the diagonal lattice), stepped with
+    # light-cone clipping (the default) and over the whole lattice
+    localized = {}
+    if rank == 0 and not args.skip_forms:
+        localized = localized_legs(qw, stream)
+
     # the other SU(2) coin classes on the benchmark workload: a real rotation and a
     # complex coin (the headline's theta = pi/4 is the Hadamard class)
     coin_classes = {}
@@ -755,7 +808,7 @@ def run_gpu(args, rank, world, local):
                         "l1_vs_f64": accuracy["l1_vs_f64_gpu"]}
         del P32, ref
 
-
+    if e2e is not None:
         del host_in, host_P
     w.close()
     return {
@@ -763,7 +816,7 @@ def run_gpu(args, rank, world, local):
         "forms": forms, "accuracy": accuracy, "e2e": e2e, "clocks": clk.summary(), "tune": tune,
         "K": K, "tile": tile, "launches": args.steps * (launches_step + 2), "dist": dist,
         "torus": torus, "batch": batch, "grad": grad_leg, "graph": graph_leg,
-        "coin_classes": coin_classes, "coin_kind": desc["coin_kind"],
+        "coin_classes": coin_classes, "coin_kind": desc["coin_kind"], "localized": localized,
     }
 
 
@@ -951,7 +1004,7 @@ def main():
         "roofline": r["roofline"], "roofline_k1": r["roofline_k1"], "cpu_baseline": cpu,
         "accuracy": r["accuracy"], "forms": r["forms"], "torus_8192": r["torus"],
         "batch_4096": r["batch"], "region_grad_1024": r["grad"], "graph": r["graph"],
-        "coin_classes": r["coin_classes"],
+        "coin_classes": r["coin_classes"], "localized_start": r["localized"],
         "norm": r["norm"], "autotune": r["tune"],
     }
     print(json.dumps(out))

@@ -201,6 +201,24 @@ qw_status qw_get_plan_ex(const qw_walk *w, int *depth_k, int *tile, int *variant
  * receives a one-line JSON summary, truncated to report_len bytes. */
 qw_status qw_autotune(qw_walk *w, char *report, size_t report_len);
 
+/* Light-cone clipping (the computation window of the paper's line walk,
+ * Sec. 3: a walker started at one site is stepped only on the window
+ * [MP - ES - i, MP + ES + i] its light cone has reached after i steps; the
+ * complexity analysis of Sec. 3.1 counts (2i + 1)^2 sites in 2D).  With
+ * clipping on (the default), qw_set_state searches the bounding box of the
+ * state's nonzero amplitudes on the GPU, and on the periodic cycle or torus
+ * without broken links every step kernel then runs only on that box widened
+ * by its steps, until the box covers the lattice.  The first qw_step or
+ * qw_step_adjoint after qw_set_state waits for the search (not for other
+ * queued work).  A dense state costs about one wave of the search.  Every
+ * amplitude equals that of stepping the whole lattice with the same plan, bit
+ * for bit (a zero may differ in sign).  on = 0 turns it off
+ * (the current state is then stepped in full); on = 1 takes effect at the next
+ * qw_set_state.  qw_describe reports the box ("support": [x0, w, y0, h],
+ * columns [x0, x0 + w) and rows [y0, y0 + h) modulo the lattice, "full" or
+ * "pending"). */
+qw_status qw_set_clipping(qw_walk *w, int on);
+
 /* One-line JSON description of the handle: lattice, precision, the coin kind
  * the kernels specialise on ("real", "complex", "grover", "hadamard2",
  * "per_site", "phase", "hadamard_class"), the plan (k, tile), which kernel

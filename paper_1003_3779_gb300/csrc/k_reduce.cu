@@ -10,6 +10,7 @@
 // is formed in float (one rounding of 2^-24 per site) and only the running
 // norm is double: double arithmetic runs at a small fraction of the float rate
 // on this part.
+#include <algorithm>
 #include <type_traits>
 
 #include "qw_internal.cuh"
@@ -125,6 +126,77 @@ cudaError_t launch_marginals(int prec, View v, int64_t ns, void *P, int p_f32, d
         case P_COMP: return marginals_t<P_COMP>(v, ns, P, p_f32, partials, nblocks, norm_dev, s);
     }
     return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------- support box
+// Bounding box of the nonzero amplitudes of a state (any coin, any plane):
+// box[0..1] the smallest and largest column, box[2..3] the smallest and
+// largest row, as unsigned 64-bit values for the atomics; box[0] > box[1]
+// means the state is zero.  It is the starting window of the light-cone
+// clipping of a localised walk (the "line" computation window of Sec. 3,
+// which starts at the walker's site and widens by one site per step).
+//
+// Work is split into tiles of SUP_THREADS consecutive sites of one row.
+// Blocks run tiles in a probe order that starts with the first tile of row 0
+// and the last tile of the last row: a dense state fills the box there, and
+// every block that then finds the box full returns, so a dense state costs
+// about one wave of tiles, a localised one a full read.
+static constexpr int SUP_THREADS = 256;
+
+__global__ void k_support_init(unsigned long long *box) {
+    box[0] = ~0ull; box[1] = 0ull; box[2] = ~0ull; box[3] = 0ull;
+}
+
+template <int P>
+__global__ void __launch_bounds__(SUP_THREADS)
+k_support(View v, int64_t nx, int64_t ny, int64_t tiles_per_row, int64_t ntiles, unsigned long long *box) {
+    using S = St<P>;
+    const int lane = threadIdx.x & 31;
+    for (int64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        {   // the box already spans the lattice: nothing left to find
+            const volatile unsigned long long *vb = box;
+            if (vb[0] == 0ull && vb[1] == (unsigned long long)(nx - 1) && vb[2] == 0ull &&
+                vb[3] == (unsigned long long)(ny - 1))
+                return;
+        }
+        const int64_t t = ti == 0 ? 0 : (ti == 1 ? ntiles - 1 : ti - 1);   // probe order
+        const int64_t y = t / tiles_per_row;
+        const int64_t x = (t - y * tiles_per_row) * SUP_THREADS + threadIdx.x;
+        bool nz = false;
+        if (x < nx) {
+            const int64_t i = y * nx + x;
+            for (int c = 0; c < v.d; ++c) {
+                const auto a = S::ld(v, c, i);
+                // (a NaN compares unequal to zero too: it counts as nonzero)
+                if constexpr (P == P_COMP)
+                    nz = nz || a.re.hi != 0.f || a.im.hi != 0.f || a.re.lo != 0.f || a.im.lo != 0.f;
+                else
+                    nz = nz || a.re != 0 || a.im != 0;
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, nz);
+        if (m && lane == 0) {
+            const int64_t xw = x;   // lane 0's column; the warp's lowest / highest set lanes
+            atomicMin(&box[0], (unsigned long long)(xw + (__ffs(m) - 1)));
+            atomicMax(&box[1], (unsigned long long)(xw + (31 - __clz(m))));
+            atomicMin(&box[2], (unsigned long long)y);
+            atomicMax(&box[3], (unsigned long long)y);
+        }
+    }
+}
+
+cudaError_t launch_support(int prec, View v, int64_t nx, int64_t ny, unsigned long long *box, cudaStream_t s) {
+    k_support_init<<<1, 1, 0, s>>>(box);
+    const int64_t tpr = (nx + SUP_THREADS - 1) / SUP_THREADS, nt = tpr * ny;
+    const unsigned grid = (unsigned)std::min<int64_t>(nt, 152 * 8);
+    switch (prec) {
+        case P_F64: k_support<P_F64><<<grid, SUP_THREADS, 0, s>>>(v, nx, ny, tpr, nt, box); break;
+        case P_F32: k_support<P_F32><<<grid, SUP_THREADS, 0, s>>>(v, nx, ny, tpr, nt, box); break;
+        case P_BF16: k_support<P_BF16><<<grid, SUP_THREADS, 0, s>>>(v, nx, ny, tpr, nt, box); break;
+        case P_COMP: k_support<P_COMP><<<grid, SUP_THREADS, 0, s>>>(v, nx, ny, tpr, nt, box); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- import / export

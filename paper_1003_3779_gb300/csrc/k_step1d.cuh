@@ -119,18 +119,17 @@ __device__ __forceinline__ int64_t tile_origin(int64_t out0, int K) {
     return t >= 0 ? t - t % VEC : -((-t + VEC - 1) / VEC) * VEC;
 }
 
-// One warp tile: K steps on the 32R sites around outputs [tile*W, tile*W + W).
-// Called by the cycle kernel below and by the batched kernel (one walk per CTA).
+// One warp tile: K steps on the 32R sites around the wthis outputs
+// [out0, out0 + wthis), a range inside [0, n).  Called by the cycle kernel
+// below and by the batched kernel (one walk per CTA).
 template <int P, int R, int CK, int FF, int ADJ>
-__device__ __forceinline__ void tb_tile(View in, View out, int64_t n, int K, int64_t W, int64_t tile, int lane,
+__device__ __forceinline__ void tb_tile(View in, View out, int64_t n, int K, int64_t out0, int wthis, int lane,
                                         const CoinP<typename St<P>::real> &cp,
                                         const Cx<typename St<P>::real> *__restrict__ coins,
                                         typename St<P>::real pre0, typename St<P>::real pre1,
                                         typename St<P>::real post0, typename St<P>::real post1) {
     using real = typename St<P>::real;
     using C = Cx<real>;
-    const int64_t out0 = tile * W;
-    const int wthis = (int)min(W, n - out0);
     const int j0 = lane * R;
     const int64_t ts = tile_origin<St<P>::VEC>(out0, K);
     const int lo = (int)(out0 - ts);   // first output's tile position, in [K, K + VEC)
@@ -220,17 +219,21 @@ __device__ __forceinline__ void tb_tile(View in, View out, int64_t n, int K, int
     store_run<P, R>(out, 1, s, j0, lo, lo + wthis, a1);
 }
 
-// W output sites per warp (see tile_origin); nwarps = ceil(n / W).
+// W output sites per warp (see tile_origin) over the output range [obeg, oend)
+// inside [0, n) (the whole cycle, or the light-cone window of a localised
+// state); nwarps = ceil((oend - obeg) / W).
 template <int P, int R, int CK, int FF, int ADJ>
 __global__ void __launch_bounds__(128)
-k_step1d(View in, View out, int64_t n, int K, int64_t W, int64_t nwarps,
+k_step1d(View in, View out, int64_t n, int K, int64_t W, int64_t obeg, int64_t oend, int64_t nwarps,
          CoinP<typename St<P>::real> cp, const Cx<typename St<P>::real> *__restrict__ coins,
          typename St<P>::real pre0, typename St<P>::real pre1,
          typename St<P>::real post0, typename St<P>::real post1) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (warp >= nwarps) return;  // uniform per warp
-    tb_tile<P, R, CK, FF, ADJ>(in, out, n, K, W, warp, lane, cp, coins, pre0, pre1, post0, post1);
+    const int64_t out0 = obeg + warp * W;
+    tb_tile<P, R, CK, FF, ADJ>(in, out, n, K, out0, (int)min(W, oend - out0), lane, cp, coins, pre0, pre1, post0,
+                               post1);
 }
 
 // ---------------------------------------------------------------- k = 1

@@ -194,10 +194,13 @@ __device__ void step2d_site(View in, View out, int64_t nx, int64_t ny, int64_t x
     }
 }
 
+// Warp gw runs row (r0 + gw / ng) mod ny, segment (g0 + gw mod ng) mod segs of
+// that row (segments of 32R sites): the whole torus, or the rows and segments
+// around the light-cone window of a localised state.
 template <int P, int R, int CK, int SH, int ADJ>
 __global__ void __launch_bounds__(128)
-k_step2d(View in, View out, int64_t nx, int64_t ny, int64_t segs, int64_t nwarps,
-         CoinP<typename St<P>::real> cp, const float *__restrict__ phi,
+k_step2d(View in, View out, int64_t nx, int64_t ny, int64_t segs, int64_t r0, int64_t nr, int64_t g0, int64_t ng,
+         int64_t nwarps, CoinP<typename St<P>::real> cp, const float *__restrict__ phi,
          const Cx<typename St<P>::real> *__restrict__ coins, typename St<P>::real gain) {
     using real = typename St<P>::real;
     using S = St<P>;
@@ -205,8 +208,11 @@ k_step2d(View in, View out, int64_t nx, int64_t ny, int64_t segs, int64_t nwarps
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gw >= nwarps) return;  // uniform per warp
-    const int64_t y = gw / segs;
-    const int64_t x0 = (gw - y * segs) * (32 * R);
+    const int64_t ry = gw / ng;
+    int64_t y = r0 + ry, seg = g0 + (gw - ry * ng);
+    if (y >= ny) y -= ny;
+    if (seg >= segs) seg -= segs;
+    const int64_t x0 = seg * (32 * R);
     const int64_t xs = x0 + lane * R;
     const int64_t row = y * nx;
 

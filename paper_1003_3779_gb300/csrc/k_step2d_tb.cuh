@@ -85,10 +85,14 @@ __device__ __forceinline__ uint4 pack2(const Cx<float> (&v)[2]) {
                       __float_as_uint(v[1].im));
 }
 
+// The outputs are the box of columns [ox0, ox0 + ow) and rows [oy0, oy0 + oh)
+// (modulo the torus): the whole torus, or the light-cone window of a localised
+// state after the launch's KT steps.
 template <int P, int KT, int CK, int SH>
 __global__ void __launch_bounds__(128)
-k_step2d_tb(View in, View out, int64_t nx, int64_t ny, int64_t W, int64_t nstrips, int64_t H, int64_t nchunks,
-            CoinP<typename St<P>::real> cp, typename St<P>::real gain) {
+k_step2d_tb(View in, View out, int64_t nx, int64_t ny, int64_t ox0, int64_t ow, int64_t oy0, int64_t oh, int64_t W,
+            int64_t nstrips, int64_t H, int64_t nchunks, CoinP<typename St<P>::real> cp,
+            typename St<P>::real gain) {
     using S = St<P>;
     using real = typename S::real;
     using C = Cx<real>;
@@ -103,10 +107,10 @@ k_step2d_tb(View in, View out, int64_t nx, int64_t ny, int64_t W, int64_t nstrip
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gw >= nstrips * nchunks) return;   // uniform per warp
     const int64_t strip = gw % nstrips, chunk = gw / nstrips;
-    const int64_t xo = strip * W;                       // first output column
-    const int wthis = (int)min(W, nx - xo);
-    const int64_t y0 = chunk * H;
-    const int64_t hthis = min(H, ny - y0);
+    const int64_t xo = ox0 + strip * W;                 // first output column (wrapped below)
+    const int wthis = (int)min(W, ow - strip * W);
+    const int64_t y0 = oy0 + chunk * H;                 // first output row (wrapped below)
+    const int64_t hthis = min(H, oh - chunk * H);
     const int j0 = lane * R;                            // tile column of the lane's first site
     const int64_t xs = xo - KT + j0;                    // its global column (may wrap)
     const bool vec = (xs >= 0) && (xs + R <= nx) && (xs % S::VEC == 0) && (R % S::VEC == 0);

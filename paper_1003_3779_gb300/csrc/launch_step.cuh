@@ -58,10 +58,12 @@ inline int64_t outputs_per_warp(int R, int K) {
 template <int P, int R, int CK, int FF, int ADJ>
 static void go1d(const Step1DArgs &a, const CoinP<typename St<P>::real> &cp, cudaStream_t s) {
     const int64_t W = outputs_per_warp<P>(R, a.K);
-    const int64_t nwarps = (a.n + W - 1) / W;
+    const bool win = a.oend > a.obeg;   // a light-cone window, else the whole cycle
+    const int64_t ob = win ? a.obeg : 0, oe = win ? a.oend : a.n;
+    const int64_t nwarps = (oe - ob + W - 1) / W;
     const int64_t blocks = (nwarps + 3) / 4;
     k_step1d<P, R, CK, FF, ADJ><<<(unsigned)blocks, 128, 0, s>>>(
-        a.in, a.out, a.n, a.K, W, nwarps, cp,
+        a.in, a.out, a.n, a.K, W, ob, oe, nwarps, cp,
         static_cast<const Cx<typename St<P>::real> *>(a.coins),
         real_from_double<typename St<P>::real>(a.pre0), real_from_double<typename St<P>::real>(a.pre1),
         real_from_double<typename St<P>::real>(a.post0), real_from_double<typename St<P>::real>(a.post1));
@@ -182,7 +184,7 @@ cudaError_t step1d_t(const Step1DArgs &a0, const void *coinp, int adj, cudaStrea
     a.tile = tile1d_effective<P>(a.tile, a.kind, adj);
     if (a.K < 1 || a.K > max_k_1d(a.tile)) return cudaErrorInvalidValue;
     const bool ff = a.shift == QW_SHIFT_FLIPFLOP;
-    if (a.K == 1) {   // one step per launch: the streaming kernel
+    if (a.K == 1 && a.oend <= a.obeg) {   // one step per launch over the whole cycle: the streaming kernel
         const bool ok = adj ? go1d_k1_kind<P, 1>(a, cp, s) : go1d_k1_kind<P, 0>(a, cp, s);
         return ok ? cudaGetLastError() : cudaErrorInvalidValue;
     }
@@ -210,10 +212,27 @@ static void go2d(const Step2DArgs &a, const CoinP<typename St<P>::real> &cp, cud
     // (the step is latency-bound at 1024^2: 17.7 against 20.5 us per step with four)
     constexpr int R = (CK == CK_PHASE && P == P_F32) ? 2 : Tile2D<P>::R;
     const int64_t segs = (a.nx + 32 * R - 1) / (32 * R);
-    const int64_t nwarps = segs * a.ny;
+    // Rows and row segments to run.  A warp reads its row and writes planes to
+    // the rows above and below; x-moving planes arrive from the neighbouring
+    // columns.  So a state supported on the box [bx0, bx0 + bw) x [by0, by0 + bh)
+    // needs the rows and columns of the box widened by one on each side (the
+    // adjoint pulls from the same neighbours): every other output is zero and
+    // already zero in the output buffer.
+    int64_t r0 = 0, nr = a.ny, g0 = 0, ng = segs;
+    if (a.bw > 0) {
+        if (a.bh + 2 < a.ny) { r0 = (a.by0 - 1 + a.ny) % a.ny; nr = a.bh + 2; }
+        if (a.bw + 2 < a.nx) {
+            // columns [c0, c0 + cw) modulo nx; the last segment of a row may be short
+            const int64_t c0 = (a.bx0 - 1 + a.nx) % a.nx, cw = a.bw + 2, S = 32 * R;
+            g0 = c0 / S;
+            ng = c0 + cw <= a.nx ? (c0 + cw - 1) / S - g0 + 1 : (segs - g0) + (c0 + cw - a.nx - 1) / S + 1;
+            ng = std::min<int64_t>(segs, ng);
+        }
+    }
+    const int64_t nwarps = ng * nr;
     const int64_t blocks = (nwarps + 3) / 4;
     k_step2d<P, R, CK, FF, ADJ><<<(unsigned)blocks, 128, 0, s>>>(
-        a.in, a.out, a.nx, a.ny, segs, nwarps, cp, a.phi,
+        a.in, a.out, a.nx, a.ny, segs, r0, nr, g0, ng, nwarps, cp, a.phi,
         static_cast<const Cx<typename St<P>::real> *>(a.coins),
         real_from_double<typename St<P>::real>(a.gain));
 }

@@ -326,6 +326,73 @@ static qw_status ensure_staging(qw_walk *w, size_t bytes) {
 
 static constexpr size_t STAGE_CHUNK = size_t(32) << 20;  // bytes per host conversion chunk
 
+// ---------------------------------------------------------------- light-cone clipping
+// A walker started on a few sites (the line computations of Sec. 3 start at
+// one site, MP, and step only the window that its light cone has reached) is
+// zero outside a box that widens by one site per step on each side.  The box
+// of the state set by qw_set_state is searched on the GPU (launch_support);
+// the steps then run on the box widened by their depth, and the box grows
+// with them until it covers the lattice.  Both state buffers are zero outside
+// the box (the other buffer is cleared once, before the first clipped step),
+// and each output is computed by the same arithmetic as in a full launch, so
+// the results equal those of the full launches bit for bit.
+
+// Queue the search for the support box of the current state (qw_set_state).
+static qw_status queue_support(qw_walk *w) {
+    w->next_clear = false;
+    if (!w->clip_on || w->bc != QW_BC_PERIODIC || links_on(w)) { w->sup_mode = 0; return QW_OK; }
+    cudaError_t e = launch_support(w->prec == QW_F64 ? P_F64 : w->prec == QW_F32 ? P_F32
+                                   : w->prec == QW_F32_BF16STORE ? P_BF16 : P_COMP,
+                                   cur_view(w), w->nx, w->ny, w->sup_dev, w->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w->sup_host, w->sup_dev, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, w->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(w->sup_ev, w->stream);
+    if (e != cudaSuccess) { w->sup_mode = 0; return cuda_error(w, e, "support search"); }
+    w->sup_mode = 1;
+    return QW_OK;
+}
+
+// Take the searched box (waits for the search only, not for later work).
+static qw_status resolve_support(qw_walk *w) {
+    if (w->sup_mode != 1) return QW_OK;
+    w->sup_mode = 0;
+    cudaError_t e = cudaEventSynchronize(w->sup_ev);
+    if (e != cudaSuccess) return cuda_error(w, e, "support search");
+    const unsigned long long *b = w->sup_host;
+    if (b[0] > b[1] || b[2] > b[3]) return QW_OK;   // a zero state: stepped in full
+    w->bx0 = (int64_t)b[0]; w->bw = (int64_t)(b[1] - b[0]) + 1;
+    w->by0 = (int64_t)b[2]; w->bh = (int64_t)(b[3] - b[2]) + 1;
+    if (w->bw >= w->nx) { w->bx0 = 0; w->bw = w->nx; }
+    if (w->bh >= w->ny) { w->by0 = 0; w->bh = w->ny; }
+    w->sup_mode = (w->bw < w->nx || w->bh < w->ny) ? 2 : 0;
+    return QW_OK;
+}
+
+// The box after K more steps.
+static void grow_support(qw_walk *w, int K) {
+    if (w->sup_mode != 2) return;
+    if (w->bw < w->nx) {
+        w->bw += 2 * (int64_t)K;
+        w->bx0 = ((w->bx0 - K) % w->nx + w->nx) % w->nx;
+        if (w->bw >= w->nx) { w->bx0 = 0; w->bw = w->nx; }
+    }
+    if (w->bh < w->ny) {
+        w->bh += 2 * (int64_t)K;
+        w->by0 = ((w->by0 - K) % w->ny + w->ny) % w->ny;
+        if (w->bh >= w->ny) { w->by0 = 0; w->bh = w->ny; }
+    }
+    if (w->bw >= w->nx && w->bh >= w->ny) w->sup_mode = 0;
+}
+
+// Before a clipped step: the other buffer must be zero outside the box.
+static qw_status clear_next(qw_walk *w) {
+    if (w->next_clear) return QW_OK;
+    cudaError_t e = cudaMemsetAsync(w->buf[w->cur ^ 1], 0, w->state_bytes, w->stream);
+    if (e != cudaSuccess) return cuda_error(w, e, "clear");
+    w->next_clear = true;
+    return QW_OK;
+}
+
 qw_status run_steps(qw_walk *w, int64_t T, int adj) {
     if (T < 0) return set_error(w, QW_EINVAL, "T must be >= 0");
     if (T == 0) return QW_OK;
@@ -336,6 +403,13 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
         if (w->kind == CK_PHASE && !(w->prec == QW_F32 || w->prec == QW_F64)) generic = true;
     }
     cudaError_t e = cudaSuccess;
+    if (generic) {
+        w->sup_mode = 0;   // the generic kernels step the whole lattice
+    } else {
+        qw_status st = resolve_support(w);
+        if (st != QW_OK) return st;
+        if (w->sup_mode == 2 && (st = clear_next(w)) != QW_OK) return st;
+    }
     if (generic) {
         StepGenericArgs a{};
         a.ndim = w->ndim; a.nx = w->nx; a.ny = w->ny; a.shift = w->shift; a.bc = w->bc;
@@ -366,13 +440,30 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
         a.n = w->nx; a.shift = w->shift; a.kind = w->kind; a.coins = w->coins_dev;
         for (int64_t rem = T; rem > 0;) {
             a.K = (int)std::min<int64_t>(K, rem);
-            // the last, shorter launch of a sweep plan falls back to the tile kernel if needed
-            a.variant = (variant == 1 && sweep_ok(w, a.K, tile)) ? 1 : 0;
+            const bool clip = w->sup_mode == 2;
+            // the last, shorter launch of a sweep plan falls back to the tile kernel
+            // if needed; a clipped launch always runs the tiles
+            a.variant = (!clip && variant == 1 && sweep_ok(w, a.K, tile)) ? 1 : 0;
             a.tile = a.variant == 1 ? tile : teff;
             if (a.variant == 0) a.K = std::min(a.K, 8 * teff);
             launch_gains_1d(w, a.K, adj, a, true, rem - a.K == 0);
             a.in = cur_view(w); a.out = next_view(w);
-            if ((e = step1d(w->prec, a, cp, adj, w->stream)) != cudaSuccess) return cuda_error(w, e, "1D step launch");
+            a.obeg = a.oend = 0;
+            const int64_t n = w->nx, len = w->bw + 2 * (int64_t)a.K;
+            if (!clip || len >= n) {
+                e = step1d(w->prec, a, cp, adj, w->stream);
+            } else {
+                // the outputs: the support widened by K, as one or two ranges inside [0, n)
+                const int64_t b0 = ((w->bx0 - a.K) % n + n) % n;
+                a.obeg = b0; a.oend = std::min(n, b0 + len);
+                e = step1d(w->prec, a, cp, adj, w->stream);
+                if (e == cudaSuccess && b0 + len > n) {
+                    a.obeg = 0; a.oend = b0 + len - n;
+                    e = step1d(w->prec, a, cp, adj, w->stream);
+                }
+            }
+            if (e != cudaSuccess) return cuda_error(w, e, "1D step launch");
+            grow_support(w, a.K);
             w->cur ^= 1;
             rem -= a.K;
         }
@@ -381,6 +472,11 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
     Step2DArgs a{};
     a.nx = w->nx; a.ny = w->ny; a.shift = w->shift; a.kind = w->kind; a.coins = w->coins_dev;
     a.phi = w->phi_dev; a.K = 1;
+    // the support box of the launch's input (bw = 0: the whole torus)
+    auto set_box = [&](Step2DArgs &b) {
+        if (w->sup_mode == 2) { b.bx0 = w->bx0; b.bw = w->bw; b.by0 = w->by0; b.bh = w->bh; }
+        else { b.bx0 = b.by0 = b.bh = 0; b.bw = 0; }
+    };
     int K2, t2;
     effective_plan(w, K2, t2);
     if (!adj && K2 > 1 && step2d_tb_ok(w->prec, w->kind, K2, w->shift)) {
@@ -390,7 +486,9 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
         while (T >= K2) {
             b.gain = drift_gain(w, K2, T - K2 == 0);   // applied once, to the launch's output
             b.in = cur_view(w); b.out = next_view(w);
+            set_box(b);
             if ((e = launch_step2d_tb(b, cp, w->stream)) != cudaSuccess) return cuda_error(w, e, "2D blocked step launch");
+            grow_support(w, K2);
             w->cur ^= 1;
             T -= K2;
         }
@@ -398,7 +496,9 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
     for (int64_t t = 0; t < T; ++t) {
         a.gain = drift_gain(w, 1, t + 1 == T);
         a.in = cur_view(w); a.out = next_view(w);
+        set_box(a);
         if ((e = step2d(w->prec, a, cp, adj, w->stream)) != cudaSuccess) return cuda_error(w, e, "2D step launch");
+        grow_support(w, 1);
         w->cur ^= 1;
     }
     return QW_OK;
@@ -446,6 +546,9 @@ qw_status qw_destroy(qw_walk *w) {
     if (w->s_in) cudaStreamDestroy(w->s_in);
     if (w->s_out) cudaStreamDestroy(w->s_out);
     if (w->host_scalar) cudaFreeHost(w->host_scalar);
+    cudaFree(w->sup_dev);
+    if (w->sup_host) cudaFreeHost(w->sup_host);
+    if (w->sup_ev) cudaEventDestroy(w->sup_ev);
     delete w;
     return QW_OK;
 }
@@ -478,6 +581,9 @@ qw_status qw_create(int ndim, const int64_t *dims, int coin_dim, qw_boundary bc,
     if (e == cudaSuccess) e = dev_alloc((void **)&w->partials, sizeof(double) * marginal_blocks());
     if (e == cudaSuccess) e = dev_alloc((void **)&w->norm_dev, sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&w->host_scalar, sizeof(double) * 4);
+    if (e == cudaSuccess) e = dev_alloc((void **)&w->sup_dev, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&w->sup_host, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->sup_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemsetAsync(w->buf[0], 0, w->state_bytes, w->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(w->buf[1], 0, w->state_bytes, w->stream);
     if (e != cudaSuccess) {
@@ -628,11 +734,12 @@ qw_status qw_set_state(qw_walk *w, const void *amp, qw_cdtype dtype, int on_devi
     const View dst = cur_view(w);
     w->gain_fb = 1.0;
     w->drift_pending = 1.0;
+    w->sup_mode = 0;
     if (direct_layout(w, dtype)) {
         e = cudaMemcpy2DAsync(w->buf[w->cur], (size_t)w->pitch * w->slot_bytes, amp, plane, plane, w->d,
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, w->stream);
         if (e != cudaSuccess) return cuda_error(w, e, "state copy");
-        return QW_OK;
+        return queue_support(w);
     }
     if (w->prec == QW_F32_COMP) {  // clear the lo slots first (a complex64 input has none)
         e = cudaMemsetAsync((char *)w->buf[w->cur] + (size_t)w->d * w->pitch * w->slot_bytes, 0,
@@ -656,7 +763,7 @@ qw_status qw_set_state(qw_walk *w, const void *amp, qw_cdtype dtype, int on_devi
             if (e != cudaSuccess) return cuda_error(w, e, "state upload");
         }
     }
-    return QW_OK;
+    return queue_support(w);
 }
 
 qw_status qw_get_state(qw_walk *w, void *amp_out, qw_cdtype dtype, int on_device) {
@@ -754,6 +861,7 @@ qw_status qw_run_host_batch(qw_walk *w, int count, const void *amp_in, int64_t i
     if (!direct_layout(w, dtype))
         return set_error(w, QW_EUNSUPPORTED, "pipelined runs take complex64 states for FP32 and complex128 for FP64");
     if (count == 0) return QW_OK;
+    w->sup_mode = 0;   // arbitrary host states: every run steps the whole lattice
     const size_t plane = (size_t)w->ns * (dtype == QW_C128 ? 16 : 8);
     const size_t pb = (size_t)w->ns * (pdtype == QW_R32 ? 4 : 8);
     cudaError_t e = cudaSuccess;
@@ -903,6 +1011,13 @@ qw_status qw_get_plan_ex(const qw_walk *w, int *depth_k, int *tile, int *variant
     return QW_OK;
 }
 
+qw_status qw_set_clipping(qw_walk *w, int on) {
+    if (!w) return QW_EINVAL;
+    w->clip_on = on != 0;
+    if (!w->clip_on) w->sup_mode = 0;
+    return QW_OK;
+}
+
 qw_status qw_describe(const qw_walk *w, char *buf, size_t len) {
     if (!w || !buf || !len) return QW_EINVAL;
     static const char *kinds[] = {"real", "complex", "grover", "hadamard2", "per_site", "phase",
@@ -913,14 +1028,21 @@ qw_status qw_describe(const qw_walk *w, char *buf, size_t len) {
     const bool generic = w->bc != QW_BC_PERIODIC || links_on(w) ||
                          (w->ndim == 2 && (w->kind == CK_PERSITE ||
                                            (w->kind == CK_PHASE && !(w->prec == QW_F32 || w->prec == QW_F64))));
+    char sup[96];
+    if (w->sup_mode == 2)
+        std::snprintf(sup, sizeof sup, "[%lld, %lld, %lld, %lld]", (long long)w->bx0, (long long)w->bw,
+                      (long long)w->by0, (long long)w->bh);
+    else
+        std::snprintf(sup, sizeof sup, "\"%s\"", w->sup_mode == 1 ? "pending" : "full");
     std::snprintf(buf, len,
                   "{\"ndim\": %d, \"sites\": %lld, \"coin_dim\": %d, \"precision\": %d, \"coin_kind\": \"%s\", "
-                  "\"k\": %d, \"tile\": %d, \"path\": \"%s\", \"state_bytes\": %zu}",
+                  "\"k\": %d, \"tile\": %d, \"path\": \"%s\", \"state_bytes\": %zu, \"clipping\": %d, "
+                  "\"support\": %s}",
                   w->ndim, (long long)w->ns, w->d, w->prec, kinds[w->kind], k, t,
                   generic ? "generic"
-                          : (w->ndim == 1 ? (var == 1 ? "k_step1d_sweep" : "k_step1d")
+                          : (w->ndim == 1 ? (var == 1 && w->sup_mode != 2 ? "k_step1d_sweep" : "k_step1d")
                                           : (k > 1 && step2d_tb_ok(w->prec, w->kind, k, w->shift) ? "k_step2d_tb" : "k_step2d")),
-                  w->state_bytes);
+                  w->state_bytes, (int)w->clip_on, sup);
     return QW_OK;
 }
 

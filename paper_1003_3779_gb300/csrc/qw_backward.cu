@@ -245,7 +245,10 @@ extern "C" qw_status qw_backward(qw_walk *w, const int64_t rect[4], int64_t T, i
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(w, e, "segment flush");
     }
 
-    // leave the walk at psi_T; hand out the gradient and the loss
+    // leave the walk at psi_T; hand out the gradient and the loss (the sweep
+    // used the walk's other buffer as scratch: it is no longer zero outside
+    // the support box)
+    w->next_clear = false;
     e = cudaMemcpyAsync(w->buf[w->cur], ckpt(nseg).p, sb, cudaMemcpyDeviceToDevice, w->stream);
     if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(grad_phi, grad, gbytes, cudaMemcpyDeviceToHost, w->stream);
     if (e == cudaSuccess && loss_out)

@@ -303,7 +303,7 @@ k_batch(BatchArgs a) {
             for (int64_t tile = wid; tile < ntiles; tile += nw) {
                 const int64_t o0 = tile * W, o1 = min(o0 + W, d.n);
                 if (!all && !meets_cone(o0, o1, d.x0, r, d.n)) continue;
-                tb_tile<P, R, CK, 0, 0>(in, out, d.n, k, W, tile, lane, cp, nullptr, one, one, g, g);
+                tb_tile<P, R, CK, 0, 0>(in, out, d.n, k, o0, (int)(o1 - o0), lane, cp, nullptr, one, one, g, g);
             }
             __syncthreads();
             View t = in; in = out; out = t;

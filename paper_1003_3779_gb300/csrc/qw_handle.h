@@ -61,6 +61,21 @@ struct qw_walk {
     double *pipe_norm = nullptr;
     cudaStream_t s_in = nullptr, s_out = nullptr;
 
+    // Light-cone clipping (the growing computation window of a localised walk,
+    // Sec. 3): the bounding box of the state's support, columns [bx0, bx0 + bw)
+    // and rows [by0, by0 + bh) modulo the lattice.  sup_mode 0: the whole
+    // lattice is stepped; 1: qw_set_state has queued the box search, whose
+    // result arrives in sup_host (event sup_ev); 2: the box is known and the
+    // steps run on it, widening it by one site per step and side.  next_clear:
+    // the other state buffer is zero outside the box.
+    bool clip_on = true;
+    int sup_mode = 0;
+    int64_t bx0 = 0, bw = 0, by0 = 0, bh = 0;
+    bool next_clear = false;
+    unsigned long long *sup_dev = nullptr;    // 4 values (device)
+    unsigned long long *sup_host = nullptr;   // 4 values (pinned)
+    cudaEvent_t sup_ev = nullptr;
+
     // execution plan
     int plan_k = 0, plan_tile = 0;
     int plan_variant = -1;   // 1D kernel: -1 automatic, 0 independent warp tiles, 1 time-skewed sweep

@@ -341,6 +341,9 @@ struct Step1DArgs {
     double post0, post1; // per-plane factors applied before the store
     int variant;         // 0 independent warp tiles (halo recomputed), 1 time-skewed sweep
     int chunks;          // sweep: chunks per warp segment (0 = default)
+    // output range [obeg, oend) inside [0, n) when oend > obeg (the light-cone
+    // window of a localised state: warp tiles only); else the whole cycle
+    int64_t obeg, oend;
 };
 cudaError_t launch_step1d(int prec, const Step1DArgs &a, const void *coinp, cudaStream_t s);
 cudaError_t launch_step1d_adjoint(int prec, const Step1DArgs &a, const void *coinp, cudaStream_t s);
@@ -354,6 +357,10 @@ struct Step2DArgs {
     const float *phi;    // CK_PHASE: nsites x 4
     int K;               // temporal depth (1 = plain fused step)
     double gain;         // factor applied to every step's coin output
+    // Support of the input state (the light-cone window of a localised
+    // state): columns [bx0, bx0 + bw) and rows [by0, by0 + bh), both modulo
+    // the torus; the state is zero outside.  bw = 0: the whole torus.
+    int64_t bx0, bw, by0, bh;
 };
 cudaError_t launch_step2d(int prec, const Step2DArgs &a, const void *coinp, cudaStream_t s);
 cudaError_t launch_step2d_adjoint(int prec, const Step2DArgs &a, const void *coinp, cudaStream_t s);
@@ -387,5 +394,7 @@ cudaError_t launch_import(int prec, View dst, int64_t nsites, const void *src, i
 cudaError_t launch_export(int prec, View src, int64_t nsites, void *dst, int dst_c64,
                           int64_t first_site, int64_t count, int plane, cudaStream_t s);
 cudaError_t launch_zero_state(View v, int nslots, int slot_bytes, cudaStream_t s);
+// bounding box of the nonzero amplitudes: box[0..1] columns, box[2..3] rows
+cudaError_t launch_support(int prec, View v, int64_t nx, int64_t ny, unsigned long long *box, cudaStream_t s);
 
 }  // namespace qw

@@ -10,7 +10,13 @@ template <int KT, int CK, int SH>
 static cudaError_t go2d_tb(const Step2DArgs &a, const CoinP<float> &cp, cudaStream_t s) {
     constexpr int R = 2;
     const int64_t W = 32 * R - 2 * KT;                 // output columns per strip
-    const int64_t nstrips = (a.nx + W - 1) / W;
+    // the output box: the whole torus, or the support box widened by KT
+    int64_t ox0 = 0, ow = a.nx, oy0 = 0, oh = a.ny;
+    if (a.bw > 0) {
+        if (a.bw + 2 * KT < a.nx) { ox0 = ((a.bx0 - KT) % a.nx + a.nx) % a.nx; ow = a.bw + 2 * KT; }
+        if (a.bh + 2 * KT < a.ny) { oy0 = ((a.by0 - KT) % a.ny + a.ny) % a.ny; oh = a.bh + 2 * KT; }
+    }
+    const int64_t nstrips = (ow + W - 1) / W;
     constexpr size_t smem = step2d_tb_smem<KT, SH>();
     auto kern = k_step2d_tb<P_F32, KT, CK, SH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -30,19 +36,20 @@ static cudaError_t go2d_tb(const Step2DArgs &a, const CoinP<float> &cp, cudaStre
             per_sm = 1;
         resident = (int64_t)sms * per_sm * 4;
     }
-    int64_t H = std::min<int64_t>(a.ny, 8 * KT), best = -1;
-    for (int64_t nc = 1; nc <= (a.ny + 8 * KT - 1) / (8 * KT); ++nc) {
-        const int64_t h = (a.ny + nc - 1) / nc;
+    int64_t H = std::min<int64_t>(oh, 8 * KT), best = -1;
+    for (int64_t nc = 1; nc <= (oh + 8 * KT - 1) / (8 * KT); ++nc) {
+        const int64_t h = (oh + nc - 1) / nc;
         if (h < 8 * KT && nc > 1) break;
         const int64_t waves = (nstrips * nc + resident - 1) / resident;
         const int64_t cost = waves * (h + 2 * KT);
         if (best < 0 || cost < best) { best = cost; H = h; }
     }
-    H = std::min<int64_t>(H, a.ny);
-    const int64_t nchunks = (a.ny + H - 1) / H;
+    H = std::min<int64_t>(H, oh);
+    const int64_t nchunks = (oh + H - 1) / H;
     const int64_t nwarps = nstrips * nchunks;
     const int64_t blocks = (nwarps + 3) / 4;
-    kern<<<(unsigned)blocks, 128, smem, s>>>(a.in, a.out, a.nx, a.ny, W, nstrips, H, nchunks, cp, (float)a.gain);
+    kern<<<(unsigned)blocks, 128, smem, s>>>(a.in, a.out, a.nx, a.ny, ox0, ow, oy0, oh, W, nstrips, H, nchunks, cp,
+                                             (float)a.gain);
     return cudaGetLastError();
 }
 

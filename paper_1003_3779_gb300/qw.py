@@ -69,6 +69,7 @@ def lib():
         "qw_autotune": (I, [P, ctypes.c_char_p, S]),
         "qw_nsites": (I64, [P]),
         "qw_describe": (I, [P, ctypes.c_char_p, S]),
+        "qw_set_clipping": (I, [P, I]),
         "qw_synchronize": (I, [P]),
         "qw_backward": (I, [P, P, I64, I64, P, P, I]),
         "qw_batch_create": (I, [I, P, P, P, P, P, I, P, P]),
@@ -269,9 +270,13 @@ def qw_autotune(h):
 
 def qw_describe(h):
     import json
-    buf = ctypes.create_string_buffer(512)
-    _check(lib().qw_describe(h, buf, 512), h)
+    buf = ctypes.create_string_buffer(1024)
+    _check(lib().qw_describe(h, buf, 1024), h)
     return json.loads(buf.value.decode())
+
+
+def qw_set_clipping(h, on):
+    _check(lib().qw_set_clipping(h, int(bool(on))), h)
 
 
 def qw_synchronize(h):
@@ -444,6 +449,11 @@ class Walk:
 
     def describe(self):
         return qw_describe(self.h)
+
+    def set_clipping(self, on):
+        """Light-cone clipping of localised states (on by default; see qw_set_clipping)."""
+        qw_set_clipping(self.h, on)
+        return self
 
     def synchronize(self):
         qw_synchronize(self.h)

@@ -1,0 +1,232 @@
+"""Light-cone clipping of localised states (the growing computation window of
+the paper's line walk, Sec. 3): the clipped steps give every amplitude of the
+full-lattice steps with the same plan, bit for bit, and match the FP64 oracle;
+the support box the library tracks is the light cone."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1003_3779_gb300 import inputs
+from tests.helpers import amp_tol, maxabs
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["f64", "f32", "bf16", "comp"]
+
+
+@pytest.fixture(scope="module")
+def qw():
+    import paper_1003_3779_gb300.qw as qw
+    qw.lib()
+    return qw
+
+
+def run(qw, dims, psi0, T, clip, prec="f32", shift=0, coin=None, plan=None, adjoint=False, per_site=None,
+        phases=None, chunks=None):
+    """State and P after T steps (in `chunks` calls of qw_step when given)."""
+    w = qw.Walk(dims, prec=prec, shift=shift).set_clipping(clip)
+    if phases is not None:
+        w.set_coin_phases(coin, phases)
+    elif per_site is not None:
+        w.set_coin(per_site, per_site=True)
+    else:
+        w.set_coin(coin)
+    if plan is not None:
+        w.set_plan_ex(*plan) if len(dims) == 1 else w.set_plan(plan)
+    w.set_state(psi0)
+    for Tc in (chunks or [T]):
+        (w.step_adjoint if adjoint else w.step)(Tc)
+    desc = w.describe()
+    out = w.state()
+    P, _ = w.probabilities()
+    w.close()
+    return out, P, desc
+
+
+def same(a, b):
+    """Equal values (a zero may carry either sign)."""
+    return np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------- 1D
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("k", [1, 7, 32])
+def test_hadamard_cycle_2001_from_site_0(qw, prec, k):
+    """The small configuration (Hadamard, N = 2001, x0 = 0, T = 1000): the
+    window wraps round site 0 at once and covers the cycle at T = 1000."""
+    N, T = 2001, 1000
+    psi0 = inputs.localized_1d(N)
+    tile = 8 if prec in ("f64", "comp") else 16
+    on = run(qw, (N,), psi0, T, True, prec, coin=inputs.hadamard(), plan=(k, tile, 0))
+    off = run(qw, (N,), psi0, T, False, prec, coin=inputs.hadamard(), plan=(k, tile, 0))
+    assert same(on[0], off[0]) and same(on[1], off[1])
+    assert off[2]["support"] == "full"
+    want = oracle.evolve(psi0, inputs.hadamard(), T)
+    assert maxabs(on[0], want) < amp_tol(prec, T, k)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shift", [0, 1])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_cycle_window_grows_then_covers(qw, prec, shift, adjoint):
+    """A complex coin from x0 = 4000 on N = 5003, in calls of 40, 300 and 2400
+    steps: the support box after the second call is [x0 - 340, x0 + 340]; after
+    the third (2 * 2740 + 1 > N) it covers the cycle."""
+    N, x0 = 5003, 4000
+    C = inputs.su2(0.3, 0.4, -0.7)
+    psi0 = inputs.localized_1d(N, x0, (0.6, 0.8j))
+    plan = (24, 8 if prec in ("f64", "comp") else 16, 0)
+    kw = dict(coin=C, plan=plan, shift=shift, adjoint=adjoint)
+    on = run(qw, (N,), psi0, 0, True, prec, chunks=[40, 300], **kw)
+    off = run(qw, (N,), psi0, 0, False, prec, chunks=[40, 300], **kw)
+    assert same(on[0], off[0]) and same(on[1], off[1])
+    assert on[2]["support"] == [x0 - 340, 681, 0, 1]
+    want = oracle.evolve(psi0, C, 340, shift=shift, adjoint=adjoint)
+    assert maxabs(on[0], want) < amp_tol(prec, 340, 24)
+    on = run(qw, (N,), psi0, 0, True, prec, chunks=[40, 300, 2400], **kw)
+    off = run(qw, (N,), psi0, 0, False, prec, chunks=[40, 300, 2400], **kw)
+    assert same(on[0], off[0]) and on[2]["support"] == "full"
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_cycle_per_site_coins_clipped(qw, prec):
+    N, T, x0 = 3000, 700, 1500
+    rng = np.random.default_rng(31)
+    coins = np.stack([inputs.random_unitary(2, rng) for _ in range(N)])
+    psi0 = inputs.localized_1d(N, x0)
+    on = run(qw, (N,), psi0, T, True, prec, per_site=coins, plan=(16, 16 if prec == "f32" else 8, 0))
+    off = run(qw, (N,), psi0, T, False, prec, per_site=coins, plan=(16, 16 if prec == "f32" else 8, 0))
+    assert same(on[0], off[0])
+    assert maxabs(on[0], oracle.evolve(psi0, coins, T)) < amp_tol(prec, T)
+
+
+def test_cycle_default_plan_matches_the_full_sweep(qw):
+    """With the default plan the full walk runs the sweep kernel and the clipped
+    one the warp tiles; the two agree to rounding, and both match the oracle."""
+    N, T, x0 = 40000, 1500, 100
+    C = inputs.su2(0.3)
+    psi0 = inputs.localized_1d(N, x0)
+    on = run(qw, (N,), psi0, T, True, "f32", coin=C)
+    off = run(qw, (N,), psi0, T, False, "f32", coin=C)
+    want = oracle.evolve(psi0, C, T)
+    assert maxabs(on[0], want) < amp_tol("f32", T) and maxabs(off[0], want) < amp_tol("f32", T)
+    assert on[2]["support"] == [N - (T - x0), 2 * T + 1, 0, 1]
+
+
+def test_dense_and_wrapped_states_step_in_full(qw):
+    N = 4096
+    w = qw.Walk((N,), prec="f32").set_coin(inputs.hadamard())
+    w.set_state(inputs.random_state((2, N), seed=3)).step(5)
+    assert w.describe()["support"] == "full"
+    psi = np.zeros((2, N), dtype=complex)
+    psi[0, 2] = 0.6
+    psi[1, N - 3] = 0.8
+    w.set_state(psi).step(5)          # support {2, N-3}: its bounding box is the cycle
+    assert w.describe()["support"] == "full"
+    assert maxabs(w.state(), oracle.evolve(psi, inputs.hadamard(), 5)) < amp_tol("f32", 5)
+    w.set_state(np.zeros((2, N), dtype=complex)).step(9)
+    assert np.all(w.state() == 0)
+    w.close()
+
+
+def test_second_set_state_replaces_the_window(qw):
+    N = 5000
+    w = qw.Walk((N,), prec="f32").set_coin(inputs.hadamard()).set_plan_ex(8, 16, 0)
+    w.set_state(inputs.localized_1d(N, 100))
+    w.set_state(inputs.localized_1d(N, 3000)).step(20)
+    assert w.describe()["support"] == [2980, 41, 0, 1]
+    assert maxabs(w.state(), oracle.evolve(inputs.localized_1d(N, 3000), inputs.hadamard(), 20)) < 1e-5
+    w.close()
+
+
+# ---------------------------------------------------------------- 2D
+COINS2 = {"grover": inputs.grover(), "hh": inputs.hadamard2(),
+          "complex": inputs.random_unitary(4, np.random.default_rng(77))}
+
+
+@pytest.mark.parametrize("k", [1, 4, 8])
+@pytest.mark.parametrize("coin", list(COINS2))
+@pytest.mark.parametrize("shift", [0, 1, 2])
+@pytest.mark.parametrize("start", [(0, 0), (150, 70)])
+def test_torus_clipped_bitwise(qw, k, coin, shift, start):
+    """A 200 x 130 torus (rows and columns not multiples of the tiles), from a
+    corner (the window wraps at once) or an interior site, T = 45 (the box stays
+    inside the torus) and T = 120 (it covers both axes), the fused step (k = 1)
+    and the streaming kernel (k = 4, 8); moving, flip-flop and diagonal."""
+    Lx, Ly = 200, 130
+    C = COINS2[coin]
+    psi0 = inputs.localized_2d(Lx, start[0], start[1], (0.5, -0.5j, 0.5, 0.5j), Ly=Ly)
+    for T in (45, 120):
+        on = run(qw, (Lx, Ly), psi0, T, True, "f32", shift=shift, coin=C, plan=k)
+        off = run(qw, (Lx, Ly), psi0, T, False, "f32", shift=shift, coin=C, plan=k)
+        assert same(on[0], off[0]) and same(on[1], off[1]), T
+        want = oracle.evolve(psi0, C, T, shift=shift)
+        assert maxabs(on[0], want) < amp_tol("f32", T), T
+        if T == 45:
+            assert on[2]["support"] == [(start[0] - 45) % Lx, 91, (start[1] - 45) % Ly, 91]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_torus_clipped_precisions_and_adjoint(qw, prec, adjoint):
+    L, T = 256, 77
+    psi0 = inputs.localized_2d(L, 30, 200)
+    on = run(qw, (L, L), psi0, T, True, prec, coin=inputs.grover(), adjoint=adjoint)
+    off = run(qw, (L, L), psi0, T, False, prec, coin=inputs.grover(), adjoint=adjoint)
+    assert same(on[0], off[0]) and same(on[1], off[1])
+    want = oracle.evolve(psi0, inputs.grover(), T, adjoint=adjoint)
+    assert maxabs(on[0], want) < amp_tol(prec, T, 1)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_torus_phase_coins_clipped(qw, prec):
+    L, T = 128, 50
+    phi = inputs.region_grad_phases(L, seed=8).reshape(-1, 4).astype(np.float32)
+    psi0 = inputs.localized_2d(L, 64, 64)
+    on = run(qw, (L, L), psi0, T, True, prec, coin=inputs.grover(), phases=phi)
+    off = run(qw, (L, L), psi0, T, False, prec, coin=inputs.grover(), phases=phi)
+    assert same(on[0], off[0])
+
+
+def test_region_gradient_with_clipping(qw):
+    """The region-mass gradient (forward with checkpoints on the clipped steps,
+    then the adjoint sweep) equals the one with clipping off."""
+    import torch
+    L, T, K = 64, 40, 8
+    phi = inputs.region_grad_phases(L, seed=9).reshape(-1, 4).astype(np.float32)
+    psi0 = inputs.localized_2d(L, 20, 20)
+    rect = (16, 16, 8, 8)
+    out = []
+    for clip in (True, False):
+        w = qw.Walk((L, L), prec="f32").set_clipping(clip).set_coin_phases(inputs.grover(), phi).set_state(psi0)
+        g = torch.empty((L * L, 4), dtype=torch.float64, device="cuda")
+        loss = qw.qw_backward(w.h, rect, T, K, g)
+        out.append((loss, g.cpu().numpy(), w.state()))
+        w.close()
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+
+
+def test_torus_8192_localized_sampled(qw):
+    """The torus of the benchmark (8192^2, Grover, k = 8) from the centre for
+    T = 256: the window never covers the lattice; the whole light cone against
+    the oracle (on a torus of 2T + 1 sites a side, which the walk from its
+    centre does not wrap in T steps), zeros outside."""
+    import torch
+    L, T = 8192, 256
+    c = L // 2
+    w = qw.Walk((L, L), prec="f32").set_coin(inputs.grover()).set_plan(8)
+    full = torch.zeros((4, L, L), dtype=torch.complex64, device="cuda")
+    for k in range(4):
+        full[k, c, c] = inputs.GROVER_SPREAD_STATE[k]
+    w.set_state(full).step(T)
+    assert w.describe()["support"] == [c - T, 2 * T + 1, c - T, 2 * T + 1]
+    got = w.state(dtype=np.complex64)
+    assert np.all(got[:, : c - T, :] == 0) and np.all(got[:, c + T + 1:, :] == 0)
+    assert np.all(got[:, :, : c - T] == 0) and np.all(got[:, :, c + T + 1:] == 0)
+    M = 2 * T + 1
+    win0 = inputs.localized_2d(M, T, T)
+    want = oracle.evolve(win0, inputs.grover(), T)      # the walk never reaches the window's edge
+    sub = got[:, c - T: c + T + 1, c - T: c + T + 1].astype(np.complex128)
+    assert maxabs(sub, want) < amp_tol("f32", T)
+    w.close()
