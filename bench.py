@@ -447,6 +447,9 @@ def run_gpu(args, rank, world, local):
     desc = w.describe()
     launches_step = math.ceil(T_STEPS / K)
 
+    # one benchmark step launches the support search of qw_set_state (2 kernels:
+    # a dense state returns after one wave), the step kernels (launches_step)
+    # and the marginals with the norm (2 kernels)
     def one_step(ev_a=None, ev_b=None):
         qw.qw_set_state(w.h, dev0)
         if ev_a is not None:
@@ -814,7 +817,7 @@ def run_gpu(args, rank, world, local):
     return {
         "value": value, "elapsed": tmax, "norm": norm, "roofline": roof, "roofline_k1": roof_k1,
         "forms": forms, "accuracy": accuracy, "e2e": e2e, "clocks": clk.summary(), "tune": tune,
-        "K": K, "tile": tile, "launches": args.steps * (launches_step + 2), "dist": dist,
+        "K": K, "tile": tile, "launches": args.steps * (launches_step + 4), "dist": dist,
         "torus": torus, "batch": batch, "grad": grad_leg, "graph": graph_leg,
         "coin_classes": coin_classes, "coin_kind": desc["coin_kind"], "localized": localized,
     }
