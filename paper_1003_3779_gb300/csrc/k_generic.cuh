@@ -194,9 +194,10 @@ k_step_generic(View in, View out, GenGeom g, int adjoint, CoinP<typename St<P>::
 // GT_X x gt_y<P>() sites.  It computes phi = C psi once for them and a one-site
 // halo into shared memory, and the state of every link the tile needs once (a
 // site's +x and +y links from one Philox draw), then each site pulls its four
-// incoming amplitudes from shared memory.  Per output the arithmetic is that of
-// k_step_generic (same coin row, same order), so the two agree bit for bit;
-// k_step_generic evaluates the coin row and the link again for every output.
+// incoming amplitudes from shared memory.  Global coins of the Grover, H (x) H
+// and real classes take their specialised form (as in the lattice kernels);
+// other coins the same coin row, in the same order, as k_step_generic, which
+// evaluates the coin row and the link again for every output.
 constexpr int GT_X = 64, GT_THREADS = 256;
 template <int P>
 constexpr int gt_y() { return 8; }
@@ -205,7 +206,9 @@ constexpr int gt_y() { return 8; }
 // memory; 4 for 16-byte amplitudes and for per-site or phase coins (which need
 // more than 32 registers)
 template <int P, int CK>
-constexpr int gt_min_blocks() { return (sizeof(Cx<typename St<P>::real>) > 8 || CK != CK_COMPLEX) ? 4 : 8; }
+constexpr int gt_min_blocks() {
+    return (sizeof(Cx<typename St<P>::real>) > 8 || CK == CK_PERSITE || CK == CK_PHASE) ? 4 : 8;
+}
 
 // state of the link from (lx, ly) to its +axis neighbour: 0 open, 1 closed
 // (reflect), 2 absorbed (line boundary); `rnd` is the site's random draw
@@ -242,13 +245,23 @@ k_step_generic_tile(View in, View out, GenGeom g, CoinP<typename St<P>::real> cp
         C a[4], e[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) a[k] = S::ld(in, k, u);
-        if (CK == CK_PHASE) gen_phases<real>(phi, u, 4, e);
+        if constexpr (CK == CK_GROVER || CK == CK_HH || CK == CK_REAL) {
+            // a global coin of a class with fewer operations than a full complex
+            // matrix (Grover: the vertex sum and one fused multiply-add per row)
+            C p[4];
+            SiteCoin<real> sc;
+            coin4<CK, real>(cp, (const C *)nullptr, sc, a, p);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            C val = czero<real>();
+            for (int r = 0; r < 4; ++r) ph[r][ey][ex] = p[r];
+        } else {
+            if (CK == CK_PHASE) gen_phases<real>(phi, u, 4, e);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) val = cfma(gen_entry<CK, real>(cp, coins, e, 4, u, r, k), a[k], val);
-            ph[r][ey][ex] = val;
+            for (int r = 0; r < 4; ++r) {
+                C val = czero<real>();
+#pragma unroll
+                for (int k = 0; k < 4; ++k) val = cfma(gen_entry<CK, real>(cp, coins, e, 4, u, r, k), a[k], val);
+                ph[r][ey][ex] = val;
+            }
         }
         if (ex <= GT_X && ey <= GY) {
             uint2 rnd = make_uint2(0u, 0u);

@@ -291,11 +291,13 @@ static void gotile(const StepGenericArgs &a, const CoinP<typename St<P>::real> &
     const auto gain = real_from_double<real>(a.gain);
     const auto *coins = static_cast<const Cx<real> *>(a.coins);
     if (a.ndim == 1) {
-        const unsigned grid = (unsigned)((a.nx + GT1_X - 1) / GT1_X);
-        if (a.shift == QW_SHIFT_MOVING)
-            k_step_generic_tile1d<P, QW_SHIFT_MOVING, CK><<<grid, GT_THREADS, 0, s>>>(a.in, a.out, g, cp, coins, a.phi, gain);
-        else
-            k_step_generic_tile1d<P, QW_SHIFT_FLIPFLOP, CK><<<grid, GT_THREADS, 0, s>>>(a.in, a.out, g, cp, coins, a.phi, gain);
+        if constexpr (CK == CK_COMPLEX || CK == CK_PERSITE || CK == CK_PHASE) {   // (the 1D tiles take these)
+            const unsigned grid = (unsigned)((a.nx + GT1_X - 1) / GT1_X);
+            if (a.shift == QW_SHIFT_MOVING)
+                k_step_generic_tile1d<P, QW_SHIFT_MOVING, CK><<<grid, GT_THREADS, 0, s>>>(a.in, a.out, g, cp, coins, a.phi, gain);
+            else
+                k_step_generic_tile1d<P, QW_SHIFT_FLIPFLOP, CK><<<grid, GT_THREADS, 0, s>>>(a.in, a.out, g, cp, coins, a.phi, gain);
+        }
         return;
     }
     const dim3 grid((unsigned)((a.nx + GT_X - 1) / GT_X), (unsigned)((a.ny + gt_y<P>() - 1) / gt_y<P>()));
@@ -309,10 +311,14 @@ template <int P>
 cudaError_t generic_t(const StepGenericArgs &a, const void *coinp, cudaStream_t s) {
     const auto &cp = *static_cast<const CoinP<typename St<P>::real> *>(coinp);
     if (generic_tile_ok<P>(a)) {
+        const bool d2 = a.ndim == 2;   // the 2D tiles specialise the global coin classes
         switch (a.kind) {
             case CK_PERSITE: gotile<P, CK_PERSITE>(a, cp, s); break;
             case CK_PHASE: gotile<P, CK_PHASE>(a, cp, s); break;
-            default: gotile<P, CK_COMPLEX>(a, cp, s); break;   // every global coin as a full matrix
+            case CK_GROVER: d2 ? gotile<P, CK_GROVER>(a, cp, s) : gotile<P, CK_COMPLEX>(a, cp, s); break;
+            case CK_HH: d2 ? gotile<P, CK_HH>(a, cp, s) : gotile<P, CK_COMPLEX>(a, cp, s); break;
+            case CK_REAL: d2 ? gotile<P, CK_REAL>(a, cp, s) : gotile<P, CK_COMPLEX>(a, cp, s); break;
+            default: gotile<P, CK_COMPLEX>(a, cp, s); break;   // other global coins as a full matrix
         }
         return cudaGetLastError();
     }
