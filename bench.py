@@ -730,16 +730,37 @@ def run_gpu(args, rank, world, local):
         wg.set_state(psi_g)
         qw.qw_backward(wg.h, _in.region_rect(Lg), Tg, Kg, g_out)
         torch.cuda.synchronize()
-        t0g = time.perf_counter()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         reps = 3
+        ev[0].record(stream)
         for _ in range(reps):
             wg.set_state(psi_g)
             lossg = qw.qw_backward(wg.h, _in.region_rect(Lg), Tg, Kg, g_out)
+        ev[1].record(stream)
+        # the forward phase alone (the same clipped steps, without the checkpoint copies)
+        wg.set_state(psi_g)
+        ev[2].record(stream)
+        wg.step(Tg)
+        ev[3].record(stream)
         torch.cuda.synchronize()
-        tg = (time.perf_counter() - t0g) / reps
-        grad_leg = {"ms": tg * 1e3, "loss": lossg,
+        tg = ev[0].elapsed_time(ev[1]) / 1e3 / reps
+        tf = ev[2].elapsed_time(ev[3]) / 1e3
+        tb = max(tg - tf, 1e-9)
+        # the adjoint sweep per site-step (FP32): reads lambda and psi (32 B each),
+        # phi (16 B) and the segment accumulator (16 B), writes lambda', psi' and
+        # the accumulator (32 + 32 + 16 B)
+        bwd_bytes = 176.0 * Lg * Lg * Tg
+        grad_leg = {"ms": tg * 1e3, "loss": lossg, "forward_ms": tf * 1e3, "adjoint_ms": tb * 1e3,
                     "site_steps_per_s": 2.0 * Tg * Lg * Lg / tg,
-                    "note": "forward T steps with checkpoints + T adjoint steps, host wall clock"}
+                    "roofline": {"bound": "hbm", "kernel": "k_backward2d<f32, Grover>", "achieved": bwd_bytes / tb / 1e9,
+                                 "peak": hbm_gbs, "unit": "GB/s", "frac": bwd_bytes / tb / 1e9 / hbm_gbs,
+                                 "algorithmic_bytes_per_site_step": 176,
+                                 "note": "adjoint time = the qw_backward call minus its forward phase timed alone; "
+                                         "the sweep's working set (lambda and psi in and out, 4 x 32 MiB, phi and "
+                                         "the accumulator, 16 MiB each) is about the L2 size, so part of it is "
+                                         "served from L2 and frac can exceed 1"},
+                    "note": "forward T steps (light-cone clipped from the localised start) with checkpoints + T "
+                            "adjoint steps; CUDA events"}
         wg.close()
 
     # the walk on a general graph (Sec. 2.1), Grover coin, FP32: a random 4-regular
