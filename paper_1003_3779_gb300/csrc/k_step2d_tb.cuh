@@ -19,8 +19,9 @@
 //   is unrolled by two, so the coin output of row r+1 is written straight
 //   into the set that is free, with no copies -- and plane 2 of rows r and
 //   r-1 (two rows of delay) in a per-warp shared-memory ring of two slots;
-// - diagonal lattice: planes 0 and 2 of rows r and r-1 in the ring; planes 1
-//   and 3 come from the newest row, so nothing stays in registers.
+// - diagonal lattice: planes 0 and 2 of rows r and r-1 in the ring, stored
+//   already moved in x; planes 1 and 3 come from the newest row, so nothing
+//   stays in registers.
 // A slot is read (row r-1) and rewritten (row r+1) by the same lane in the
 // same level, so the ring needs no synchronisation.
 //
@@ -240,14 +241,17 @@ k_step2d_tb(View in, View out, int64_t nx, int64_t ny, int64_t ox0, int64_t ow, 
                     Aw[s][1][i] = N[1][i];
                 }
             } else {
-                C old0[R], old2[R];
-                S::unpack(dv[0], old0);
-                S::unpack(dv[1], old2);
-                d[0] = pack2(N[0]);
-                d[32] = pack2(N[2]);
-                from_left(old0, psi[0]);       // from (x-1, y-1)
+                // planes 0 and 2 enter the ring already moved in x, two rows
+                // before they are used, so their shuffles stay off this level's
+                // dependency chain
+                C s0[R], s2[R];
+                from_left(N[0], s0);           // to (x+1, y+1) two rows on
+                from_right(N[2], s2);          // to (x-1, y+1) two rows on
+                S::unpack(dv[0], psi[0]);      // from (x-1, y-1)
+                S::unpack(dv[1], psi[2]);      // from (x+1, y-1)
+                d[0] = pack2(s0);
+                d[32] = pack2(s2);
                 from_left(N[1], psi[1]);       // from (x-1, y+1)
-                from_right(old2, psi[2]);      // from (x+1, y-1)
                 from_right(N[3], psi[3]);      // from (x+1, y+1)
             }
             if (s + 1 < KT) {
