@@ -210,7 +210,8 @@ qw_status qw_autotune(qw_walk *w, char *report, size_t report_len);
  * without broken links every step kernel then runs only on that box widened
  * by its steps, until the box covers the lattice.  The first qw_step or
  * qw_step_adjoint after qw_set_state waits for the search (not for other
- * queued work).  A dense state costs about one wave of the search.  Every
+ * queued work); while the walk's stream is being captured into a CUDA graph
+ * nothing waits: the search is skipped and the steps run on the whole lattice.  A dense state costs about one wave of the search.  Every
  * amplitude equals that of stepping the whole lattice with the same plan, bit
  * for bit (a zero may differ in sign).  on = 0 turns it off
  * (the current state is then stepped in full); on = 1 takes effect at the next

@@ -337,10 +337,21 @@ static constexpr size_t STAGE_CHUNK = size_t(32) << 20;  // bytes per host conve
 // and each output is computed by the same arithmetic as in a full launch, so
 // the results equal those of the full launches bit for bit.
 
+// Is the walk's stream being captured into a CUDA graph?  Then nothing may
+// wait for its work: the search is skipped and the steps run in full.
+static bool capturing(const qw_walk *w) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(w->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+}
+
 // Queue the search for the support box of the current state (qw_set_state).
 static qw_status queue_support(qw_walk *w) {
     w->next_clear = false;
-    if (!w->clip_on || w->bc != QW_BC_PERIODIC || links_on(w)) { w->sup_mode = 0; return QW_OK; }
+    if (!w->clip_on || w->bc != QW_BC_PERIODIC || links_on(w) || capturing(w)) {
+        (void)cudaGetLastError();
+        w->sup_mode = 0;
+        return QW_OK;
+    }
     cudaError_t e = launch_support(w->prec == QW_F64 ? P_F64 : w->prec == QW_F32 ? P_F32
                                    : w->prec == QW_F32_BF16STORE ? P_BF16 : P_COMP,
                                    cur_view(w), w->nx, w->ny, w->sup_dev, w->stream);
@@ -356,6 +367,7 @@ static qw_status queue_support(qw_walk *w) {
 static qw_status resolve_support(qw_walk *w) {
     if (w->sup_mode != 1) return QW_OK;
     w->sup_mode = 0;
+    if (capturing(w)) { (void)cudaGetLastError(); return QW_OK; }   // step in full
     cudaError_t e = cudaEventSynchronize(w->sup_ev);
     if (e != cudaSuccess) return cuda_error(w, e, "support search");
     const unsigned long long *b = w->sup_host;

@@ -230,3 +230,29 @@ def test_torus_8192_localized_sampled(qw):
     sub = got[:, c - T: c + T + 1, c - T: c + T + 1].astype(np.complex128)
     assert maxabs(sub, want) < amp_tol("f32", T)
     w.close()
+
+
+def test_steps_captured_in_a_cuda_graph_run_in_full(qw):
+    """While the walk's stream is captured into a CUDA graph nothing may wait for
+    it: qw_set_state skips the support search and the captured steps run on the
+    whole lattice.  The replayed graph matches the oracle."""
+    import ctypes
+    import torch
+    N, T = 4096, 64
+    C = inputs.su2(0.3)
+    s = torch.cuda.Stream()
+    psi0 = inputs.localized_1d(N, 100)
+    psi = torch.from_numpy(psi0.astype(np.complex64)).cuda()
+    w = qw.Walk((N,), prec="f32", stream=ctypes.c_void_p(s.cuda_stream)).set_coin(C)
+    w.set_state(psi).step(T)          # outside a capture: clipped, kernels loaded
+    assert w.describe()["support"] != "full"
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        qw.qw_set_state(w.h, psi)
+        qw.qw_step(w.h, T)
+    g.replay()
+    torch.cuda.synchronize()
+    assert w.describe()["support"] == "full"
+    assert maxabs(w.state(), oracle.evolve(psi0, C, T)) < amp_tol("f32", T)
+    w.close()
