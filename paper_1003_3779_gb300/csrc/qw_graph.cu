@@ -228,7 +228,8 @@ k_graph_scatter(int A, const int *__restrict__ dst, const Cx<R> *__restrict__ tm
 // (pf), so that the next window's bucket is read from DRAM in order while this
 // window's random reads hit L2.  The index and output streams are marked
 // evict-first to leave L2 to the buckets.
-static constexpr int GR_GATHER = 8;   // arcs per thread of the gather pass (loads in flight)
+static constexpr int GR_GATHER = 4;   // arcs per thread of the gather pass (loads in flight; 4 measured
+                                      // fastest of 1..16 at 2^28 arcs: more fill the load queue)
 
 // L2-only load (the random reads of the gather pass gain nothing from L1)
 __device__ __forceinline__ Cx<float> ldcg(const Cx<float> *p) {
