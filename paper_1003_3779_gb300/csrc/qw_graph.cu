@@ -52,7 +52,7 @@ namespace qw {
 static constexpr int GR_THREADS = 256;
 static constexpr int GR_HEAVY = 32;
 static constexpr int GR_RED_BLOCKS = 152 * 4;
-static constexpr int GR_TILE = 1024;                       // arcs per block of the bucketing pass
+static constexpr int GR_TILE = 2048;                       // arcs per block of the bucketing pass (1024..4096 swept)
 static constexpr size_t GR_WINDOW = size_t(16) << 20;      // output bytes per bucket
 
 template <class R>
