@@ -371,18 +371,21 @@ def coin_class_leg(qw, C, dev0, stream, sm_max_mhz, hbm_gbs):
 
 def localized_legs(qw, stream):
     """Walks from one site: the diagonal lattice (H (x) H) on the 8192^2 torus
-    from its centre for T = 500, and the SU(2) theta = pi/4 line on the cycle of
-    2^27 sites from its centre for T = 4096, FP32, default plans.  Each is timed
+    from its centre for T = 500, the SU(2) theta = pi/4 walk on the cycle of 2^27
+    sites from its centre for T = 4096, and the Hadamard walk on the line of 2^27
+    sites (absorbing ends) from its centre for T = 1024, FP32, default plans.  Each is timed
     with light-cone clipping and with it off (the whole lattice every step);
     dense rates count every site of the lattice, active ones the light cone."""
     import torch
     from paper_1003_3779_gb300 import inputs as _in
     out = {}
     cases = (
-        ("diagonal_hh_8192_from_centre_T500", (8192, 8192), 500, qw.SHIFT_DIAGONAL, _in.hadamard2()),
-        ("line_su2_2e27_from_centre_T4096", (N_SITES,), T_STEPS, qw.SHIFT_MOVING, _in.su2(THETA)),
+        ("diagonal_hh_8192_from_centre_T500", (8192, 8192), 500, qw.SHIFT_DIAGONAL, _in.hadamard2(), qw.BC_PERIODIC),
+        ("cycle_su2_2e27_from_centre_T4096", (N_SITES,), T_STEPS, qw.SHIFT_MOVING, _in.su2(THETA), qw.BC_PERIODIC),
+        # the paper's line walk: absorbing ends, the generic tiled kernel
+        ("line_hadamard_2e27_from_centre_T1024", (N_SITES,), 1024, qw.SHIFT_MOVING, _in.hadamard(), qw.BC_LINE),
     )
-    for name, dims, T, shift, C in cases:
+    for name, dims, T, shift, C, bc in cases:
         d = 2 * len(dims)
         z = torch.zeros((d,) + tuple(reversed(dims)), dtype=torch.complex64, device="cuda")
         centre = tuple(n // 2 for n in reversed(dims))
@@ -392,7 +395,7 @@ def localized_legs(qw, stream):
         cone = sum(min((2 * t + 1) ** len(dims), nsites) for t in range(1, T + 1))   # light-cone site-steps
         leg = {"sites": nsites, "T": T, "active_site_steps": float(cone)}
         for clip in (True, False):
-            w = qw.Walk(dims, prec="f32", shift=shift).set_coin(C).set_clipping(clip)
+            w = qw.Walk(dims, prec="f32", shift=shift, bc=bc).set_coin(C).set_clipping(clip)
             w.set_state(z)
             w.step(16)                       # warm-up (kernels loaded, plans fixed)
             w.set_state(z)

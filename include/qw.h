@@ -206,9 +206,12 @@ qw_status qw_autotune(qw_walk *w, char *report, size_t report_len);
  * [MP - ES - i, MP + ES + i] its light cone has reached after i steps; the
  * complexity analysis of Sec. 3.1 counts (2i + 1)^2 sites in 2D).  With
  * clipping on (the default), qw_set_state searches the bounding box of the
- * state's nonzero amplitudes on the GPU, and on the periodic cycle or torus
- * without broken links every step kernel then runs only on that box widened
- * by its steps, until the box covers the lattice.  The first qw_step or
+ * state's nonzero amplitudes on the GPU, and every step kernel then runs only
+ * on that box widened by its steps, until the box covers the lattice: on the
+ * cycle and the torus the box wraps; on the segment and the line it stops at
+ * the ends (with broken links too).  The adjoint with a boundary or broken
+ * links, and per-site coins on the torus, run kernels that step the whole
+ * lattice; the box still widens with them.  The first qw_step or
  * qw_step_adjoint after qw_set_state waits for the search (not for other
  * queued work); while the walk's stream is being captured into a CUDA graph
  * nothing waits: the search is skipped and the steps run on the whole lattice.  A dense state costs about one wave of the search.  Every

@@ -20,6 +20,10 @@ struct GenGeom {
     int shift, bc;
     const uint8_t *links;
     uint32_t rthr, rk0, rk1, rstep;   // links broken at random at this step (rthr 0: none)
+    // tiled kernels: block (bx, by) runs tile ((tx0 + bx) mod ntx, (ty0 + by) mod nty)
+    // of the ntx x nty tiles of the lattice (all of them, or those around the
+    // light-cone window of a localised state)
+    int tx0, ntx, ty0, nty;
 };
 
 // Words 0 and 1 of Philox4x32 with 10 rounds (Salmon, Moraes, Dror and Shaw, SC
@@ -235,7 +239,10 @@ k_step_generic_tile(View in, View out, GenGeom g, CoinP<typename St<P>::real> cp
     __shared__ C ph[4][EY][EX];                        // phi of the tile and its halo
     __shared__ unsigned char ls[2][GY + 1][GT_X + 1];  // link states, owners from (x0 - 1, y0 - 1)
     const int nx = (int)g.nx, ny = (int)g.ny;          // both < 2^31 (launcher)
-    const int x0 = blockIdx.x * GT_X, y0 = blockIdx.y * GY;
+    int tx = g.tx0 + (int)blockIdx.x, ty = g.ty0 + (int)blockIdx.y;
+    if (tx >= g.ntx) tx -= g.ntx;
+    if (ty >= g.nty) ty -= g.nty;
+    const int x0 = tx * GT_X, y0 = ty * GY;
     for (int i = threadIdx.x; i < EX * EY; i += GT_THREADS) {
         const int ex = i % EX, ey = i / EX;
         int gx = x0 - 1 + ex, gy = y0 - 1 + ey;       // in [-1, n + GT_X]: wrap
@@ -316,7 +323,9 @@ k_step_generic_tile1d(View in, View out, GenGeom g, CoinP<typename St<P>::real> 
     __shared__ C ph[2][EX];
     __shared__ unsigned char ls[GT1_X + 1];      // links owned by x0 - 1 .. x0 + GT1_X - 1
     const int nx = (int)g.nx;                    // < 2^31 (launcher)
-    const int x0 = blockIdx.x * GT1_X;
+    int tx = g.tx0 + (int)blockIdx.x;
+    if (tx >= g.ntx) tx -= g.ntx;
+    const int x0 = tx * GT1_X;
     for (int ex = threadIdx.x; ex < EX; ex += GT_THREADS) {
         int gx = x0 - 1 + ex;
         gx = gx < 0 ? gx + nx : (gx >= nx ? gx % nx : gx);

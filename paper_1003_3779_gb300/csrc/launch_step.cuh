@@ -266,9 +266,32 @@ cudaError_t step2d_t(const Step2DArgs &a, const void *coinp, int adj, cudaStream
     return cudaGetLastError();
 }
 
+// Tiles of T sites along an axis of n sites that hold the outputs of one step
+// from a state supported on [c0, c0 + cw): that range widened by one site on
+// each side (modulo n on the periodic lattice, cut at its ends otherwise).
+// The last tile may be short.  cw = 0: every tile.
+static inline void tile_range(int64_t c0, int64_t cw, int64_t n, int T, bool periodic, int &t0, int &nt) {
+    const int64_t ntiles = (n + T - 1) / T;
+    t0 = 0;
+    nt = (int)ntiles;
+    if (cw <= 0) return;
+    int64_t a0, aw;
+    if (periodic) {
+        if (cw + 2 >= n) return;
+        a0 = (c0 - 1 + n) % n;
+        aw = cw + 2;
+    } else {
+        a0 = std::max<int64_t>(0, c0 - 1);
+        aw = std::min<int64_t>(n, c0 + cw + 1) - a0;
+    }
+    t0 = (int)(a0 / T);
+    const int64_t k = a0 + aw <= n ? (a0 + aw - 1) / T - t0 + 1 : (ntiles - t0) + (a0 + aw - n - 1) / T + 1;
+    nt = (int)std::min<int64_t>(ntiles, k);
+}
+
 template <int P, int CK>
 static void gogen(const StepGenericArgs &a, const CoinP<typename St<P>::real> &cp, cudaStream_t s) {
-    GenGeom g{a.ndim, a.nx, a.ny, a.nx * a.ny, a.shift, a.bc, a.links, a.rthr, a.rk0, a.rk1, a.rstep};
+    GenGeom g{a.ndim, a.nx, a.ny, a.nx * a.ny, a.shift, a.bc, a.links, a.rthr, a.rk0, a.rk1, a.rstep, 0, 1, 0, 1};
     const int64_t blocks = (g.ns + 127) / 128;
     k_step_generic<P, CK><<<(unsigned)blocks, 128, 0, s>>>(
         a.in, a.out, g, a.adjoint, cp, static_cast<const Cx<typename St<P>::real> *>(a.coins), a.phi,
@@ -287,12 +310,15 @@ static bool generic_tile_ok(const StepGenericArgs &a) {
 template <int P, int CK>
 static void gotile(const StepGenericArgs &a, const CoinP<typename St<P>::real> &cp, cudaStream_t s) {
     using real = typename St<P>::real;
-    GenGeom g{a.ndim, a.nx, a.ny, a.nx * a.ny, a.shift, a.bc, a.links, a.rthr, a.rk0, a.rk1, a.rstep};
+    const bool per = a.bc == QW_BC_PERIODIC;
+    GenGeom g{a.ndim, a.nx, a.ny, a.nx * a.ny, a.shift, a.bc, a.links, a.rthr, a.rk0, a.rk1, a.rstep, 0, 1, 0, 1};
     const auto gain = real_from_double<real>(a.gain);
     const auto *coins = static_cast<const Cx<real> *>(a.coins);
     if (a.ndim == 1) {
         if constexpr (CK == CK_COMPLEX || CK == CK_PERSITE || CK == CK_PHASE) {   // (the 1D tiles take these)
-            const unsigned grid = (unsigned)((a.nx + GT1_X - 1) / GT1_X);
+            tile_range(a.bx0, a.bw, a.nx, GT1_X, per, g.tx0, g.ntx);
+            const unsigned grid = (unsigned)g.ntx;
+            g.ntx = (int)((a.nx + GT1_X - 1) / GT1_X);
             if (a.shift == QW_SHIFT_MOVING)
                 k_step_generic_tile1d<P, QW_SHIFT_MOVING, CK><<<grid, GT_THREADS, 0, s>>>(a.in, a.out, g, cp, coins, a.phi, gain);
             else
@@ -300,7 +326,12 @@ static void gotile(const StepGenericArgs &a, const CoinP<typename St<P>::real> &
         }
         return;
     }
-    const dim3 grid((unsigned)((a.nx + GT_X - 1) / GT_X), (unsigned)((a.ny + gt_y<P>() - 1) / gt_y<P>()));
+    int gx = 0, gy = 0;
+    tile_range(a.bx0, a.bw, a.nx, GT_X, per, g.tx0, gx);
+    tile_range(a.by0, a.bw > 0 ? a.bh : 0, a.ny, gt_y<P>(), per, g.ty0, gy);
+    g.ntx = (int)((a.nx + GT_X - 1) / GT_X);
+    g.nty = (int)((a.ny + gt_y<P>() - 1) / gt_y<P>());
+    const dim3 grid((unsigned)gx, (unsigned)gy);
     if (a.shift == QW_SHIFT_MOVING)
         k_step_generic_tile<P, QW_SHIFT_MOVING, CK><<<grid, GT_THREADS, 0, s>>>(a.in, a.out, g, cp, coins, a.phi, gain);
     else

@@ -347,7 +347,7 @@ static bool capturing(const qw_walk *w) {
 // Queue the search for the support box of the current state (qw_set_state).
 static qw_status queue_support(qw_walk *w) {
     w->next_clear = false;
-    if (!w->clip_on || w->bc != QW_BC_PERIODIC || links_on(w) || capturing(w)) {
+    if (!w->clip_on || capturing(w)) {
         (void)cudaGetLastError();
         w->sup_mode = 0;
         return QW_OK;
@@ -380,19 +380,25 @@ static qw_status resolve_support(qw_walk *w) {
     return QW_OK;
 }
 
-// The box after K more steps.
+// The box after K more steps: one site more on each side per step, modulo the
+// lattice on the periodic one, cut at its ends on the segment and the line.
+static void grow_axis(int64_t &b0, int64_t &bw, int64_t n, int K, bool periodic) {
+    if (bw >= n) return;
+    if (periodic) {
+        bw += 2 * (int64_t)K;
+        b0 = ((b0 - K) % n + n) % n;
+    } else {
+        const int64_t lo = std::max<int64_t>(0, b0 - K), hi = std::min<int64_t>(n, b0 + bw + K);
+        b0 = lo;
+        bw = hi - lo;
+    }
+    if (bw >= n) { b0 = 0; bw = n; }
+}
 static void grow_support(qw_walk *w, int K) {
     if (w->sup_mode != 2) return;
-    if (w->bw < w->nx) {
-        w->bw += 2 * (int64_t)K;
-        w->bx0 = ((w->bx0 - K) % w->nx + w->nx) % w->nx;
-        if (w->bw >= w->nx) { w->bx0 = 0; w->bw = w->nx; }
-    }
-    if (w->bh < w->ny) {
-        w->bh += 2 * (int64_t)K;
-        w->by0 = ((w->by0 - K) % w->ny + w->ny) % w->ny;
-        if (w->bh >= w->ny) { w->by0 = 0; w->bh = w->ny; }
-    }
+    const bool per = w->bc == QW_BC_PERIODIC;
+    grow_axis(w->bx0, w->bw, w->nx, K, per);
+    grow_axis(w->by0, w->bh, w->ny, K, per);
     if (w->bw >= w->nx && w->bh >= w->ny) w->sup_mode = 0;
 }
 
@@ -415,9 +421,7 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
         if (w->kind == CK_PHASE && !(w->prec == QW_F32 || w->prec == QW_F64)) generic = true;
     }
     cudaError_t e = cudaSuccess;
-    if (generic) {
-        w->sup_mode = 0;   // the generic kernels step the whole lattice
-    } else {
+    {
         qw_status st = resolve_support(w);
         if (st != QW_OK) return st;
         if (w->sup_mode == 2 && (st = clear_next(w)) != QW_OK) return st;
@@ -438,7 +442,12 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
             if (w->link_thr && !adj) ++w->link_step;
             a.gain = drift_gain(w, 1, t + 1 == T);
             a.in = cur_view(w); a.out = next_view(w);
+            // the tiled forward kernels run only the tiles around the support box
+            // (the others, and the per-site kernel, step the whole lattice)
+            if (w->sup_mode == 2) { a.bx0 = w->bx0; a.bw = w->bw; a.by0 = w->by0; a.bh = w->bh; }
+            else { a.bx0 = a.by0 = a.bh = 0; a.bw = 0; }
             if ((e = stepgen(w->prec, a, cp, w->stream)) != cudaSuccess) return cuda_error(w, e, "generic step launch");
+            grow_support(w, 1);
             w->cur ^= 1;
         }
         return QW_OK;

@@ -380,6 +380,9 @@ struct StepGenericArgs {
     // links broken at random: closed when Philox word 0 < rthr (0: off), key
     // (rk0, rk1), step index rstep
     uint32_t rthr, rk0, rk1, rstep;
+    // support box of the input state as in Step2DArgs (modulo the lattice on
+    // the periodic one, inside it otherwise); bw = 0: the whole lattice
+    int64_t bx0, bw, by0, bh;
 };
 cudaError_t launch_step_generic(int prec, const StepGenericArgs &a, const void *coinp, cudaStream_t s);
 

@@ -256,3 +256,92 @@ def test_steps_captured_in_a_cuda_graph_run_in_full(qw):
     assert w.describe()["support"] == "full"
     assert maxabs(w.state(), oracle.evolve(psi0, C, T)) < amp_tol("f32", T)
     w.close()
+
+
+# ---------------------------------------------------------------- boundaries and links
+def _generic_run(qw, dims, psi0, T, clip, bc, shift, C, p=0.0, seed=0, fixed=None, adjoint=False, prec="f32"):
+    w = qw.Walk(dims, prec=prec, shift=shift, bc=bc).set_clipping(clip).set_coin(C)
+    if fixed is not None:
+        w.set_links(fixed)
+    if p:
+        w.set_link_noise(p, seed)
+    w.set_state(psi0)
+    (w.step_adjoint if adjoint else w.step)(T)
+    out, desc = w.state(), w.describe()
+    w.close()
+    return out, desc
+
+
+@pytest.mark.parametrize("bc", [0, 1, 2])
+@pytest.mark.parametrize("shift", [0, 1])
+@pytest.mark.parametrize("links", ["none", "fixed", "random"])
+@pytest.mark.parametrize("x0", [6, 1500, 2996])
+def test_line_and_segment_window_1d(qw, bc, shift, links, x0):
+    """The generic tiled kernel on the cycle, the segment (reflecting ends) and
+    the line (absorbing ends, the paper's line walk) with fixed or per-step
+    random broken links: clipped and full steps agree bit for bit and match the
+    oracle; on the segment and the line the window stops at the ends."""
+    N, T = 3000, 120
+    rng = np.random.default_rng(400 + bc + 3 * shift)
+    C = inputs.random_unitary(2, rng)
+    psi0 = inputs.localized_1d(N, x0, (0.6, 0.8j))
+    fixed = (rng.uniform(size=(1, N)) < 0.1).astype(np.uint8) if links == "fixed" else None
+    p, seed = (0.1, 91) if links == "random" else (0.0, 0)
+    kw = dict(bc=bc, shift=shift, C=C, p=p, seed=seed, fixed=fixed)
+    on, desc = _generic_run(qw, (N,), psi0, T, True, **kw)
+    off, _ = _generic_run(qw, (N,), psi0, T, False, **kw)
+    assert same(on, off)
+    assert desc["path"] == ("k_step1d" if bc == 0 and links == "none" else "generic")
+    lo, hi = x0 - T, x0 + T + 1
+    if bc == 0:
+        assert desc["support"] == [lo % N, 2 * T + 1, 0, 1]
+    else:
+        assert desc["support"] == [max(0, lo), min(N, hi) - max(0, lo), 0, 1]
+    closed = fixed
+    if links == "random":
+        closed = oracle.link_masks((N,), seed, p, 0, T)
+    want = oracle.evolve(psi0, C, T, shift=shift, bc=bc, closed=closed, closed_per_step=links == "random")
+    assert maxabs(on, want) < amp_tol("f32", T)
+
+
+@pytest.mark.parametrize("bc", [0, 1, 2])
+@pytest.mark.parametrize("shift", [0, 1])
+@pytest.mark.parametrize("links", ["none", "fixed", "random"])
+@pytest.mark.parametrize("start", [(1, 2), (100, 60), (198, 128)])
+def test_line_and_segment_window_2d(qw, bc, shift, links, start):
+    """The same on a 200 x 130 lattice (the generic 64 x 8 tiles; rows and
+    columns not multiples of the tile), from next to a corner, the interior and
+    the far corner, T = 40."""
+    Lx, Ly, T = 200, 130, 40
+    rng = np.random.default_rng(500 + bc + 3 * shift)
+    C = inputs.grover() if links == "none" else inputs.random_unitary(4, rng)
+    psi0 = inputs.localized_2d(Lx, start[0], start[1], (0.5, -0.5j, 0.5, 0.5j), Ly=Ly)
+    fixed = (rng.uniform(size=(2, Lx * Ly)) < 0.1).astype(np.uint8) if links == "fixed" else None
+    p, seed = (0.1, 92) if links == "random" else (0.0, 0)
+    kw = dict(bc=bc, shift=shift, C=C, p=p, seed=seed, fixed=fixed)
+    on, desc = _generic_run(qw, (Lx, Ly), psi0, T, True, **kw)
+    off, _ = _generic_run(qw, (Lx, Ly), psi0, T, False, **kw)
+    assert same(on, off)
+    closed = fixed
+    if links == "random":
+        closed = oracle.link_masks((Ly, Lx), seed, p, 0, T)
+    want = oracle.evolve(psi0, C, T, shift=shift, bc=bc, closed=closed, closed_per_step=links == "random")
+    assert maxabs(on, want) < amp_tol("f32", T)
+    if bc != 0:
+        x0, y0 = start
+        assert desc["support"] == [max(0, x0 - T), min(Lx, x0 + T + 1) - max(0, x0 - T),
+                                   max(0, y0 - T), min(Ly, y0 + T + 1) - max(0, y0 - T)]
+
+
+@pytest.mark.parametrize("bc", [1, 2])
+def test_line_window_adjoint_steps_in_full(qw, bc):
+    """The adjoint with a boundary runs the per-site generic kernel over the
+    whole lattice; the tracked window still widens with it, and clipped and
+    full runs agree."""
+    N, T, x0 = 2000, 90, 40
+    C = inputs.su2(0.3, 0.2, -0.1)
+    psi0 = inputs.localized_1d(N, x0)
+    on, desc = _generic_run(qw, (N,), psi0, T, True, bc=bc, shift=0, C=C, adjoint=True)
+    off, _ = _generic_run(qw, (N,), psi0, T, False, bc=bc, shift=0, C=C, adjoint=True)
+    assert same(on, off) and desc["support"] == [0, x0 + T + 1, 0, 1]
+    assert maxabs(on, oracle.evolve(psi0, C, T, bc=bc, adjoint=True)) < amp_tol("f32", T)
