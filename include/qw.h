@@ -348,7 +348,10 @@ qw_status qw_gwalk_probabilities(qw_gwalk *g, void *P_out, qw_rdtype pdtype, int
  * L2-resident window by scattered writes (2) or gathered reads (3)); -1
  * restores the default (push).  Every form gives the same bits.  Forms 2 and 3
  * build tables on first use (host work O(arcs); device memory 14 bytes per arc
- * plus one more state buffer). */
+ * plus one more state buffer).  On graphs of degree 2 or 4, a qw_gwalk_step
+ * call of T >= 2 steps in form 3 fuses each step's gather with the next
+ * step's coin and bucketing (T + 1 passes); it uses the input state buffer as
+ * scratch, so a launch error in that call leaves no valid state. */
 qw_status qw_gwalk_set_variant(qw_gwalk *g, int variant);
 
 /* Output bytes each destination bucket of forms 2 and 3 covers (default

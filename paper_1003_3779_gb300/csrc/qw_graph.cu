@@ -31,6 +31,10 @@
 //   pass 2 moves each bucket to its final places, which all lie in one window
 //     small enough to stay in L2: scattered writes (variant 2) or gathered
 //     reads (variant 3) hit L2, and DRAM sees whole lines.
+// On graphs of degree 2 or 4 the gather form runs the gather of one step and
+// the bucketing of the next as one pass (the state stays bucketed between the
+// steps of a call): T steps take T + 1 passes, not 2T, and psi is written and
+// read back once per call instead of once per step.
 // Which form is fastest for a graph is measured (qw_gwalk_autotune).
 //
 // Regular graphs of degree 2 or 4 find an arc's vertex by division; others
@@ -268,6 +272,63 @@ k_graph_gather(int A, const int *__restrict__ srcs, const Cx<R> *__restrict__ tm
             __stcs(reinterpret_cast<double2 *>(out + a), make_double2(v[k].re, v[k].im));
         }
     }
+}
+
+// Steps t and t + 1 of the gather form fused, on regular graphs: a thread per
+// vertex gathers psi_t of the vertex's arcs from the bucketed phi of step t - 1
+// (the same L2-resident window reads as k_graph_gather), applies the coin of
+// step t, and the tile is bucketed for the next gather as in k_graph_bucket.
+// psi_t itself never goes to memory; the values that reach the coin are the
+// ones the two separate passes would store and reload, so the result is the
+// same to the bit.  GF_GATHERS gathers in flight per thread per round (swept
+// at 2^28 arcs: 256 threads x 4 gathers 1.80 ms per step; x 8 gathers 1.99;
+// 128 threads x 8 or 16 gathers 2.04 / 2.21; 8 blocks per SM forced: 1.79).
+static constexpr int GF_THREADS = 256, GF_GATHERS = 4, GF_MIN_BLOCKS = 1;
+template <class R, int MODE, int DR>
+__global__ void __launch_bounds__(GF_THREADS, GF_MIN_BLOCKS)
+k_graph_gather_bucket(GraphArgs<R> g, const Cx<R> *__restrict__ tin, const int *__restrict__ srcs,
+                      const unsigned short *__restrict__ lpos, const int *__restrict__ gsl, Cx<R> *__restrict__ tout,
+                      int pf) {
+    static_assert(DR == 2 || DR == 4, "regular graphs of degree 2 or 4");
+    constexpr int UV = GF_GATHERS / DR;      // vertices per thread per round
+    __shared__ Cx<R> sm[GR_TILE];
+    const int base = blockIdx.x * GR_TILE;   // < A: the grid has ceil(A / GR_TILE) blocks
+    const int n = min(GR_TILE, g.A - base);  // a multiple of DR (GR_TILE is, and so is A)
+    const int nv = n / DR;
+    for (int v0 = threadIdx.x; v0 < nv; v0 += GF_THREADS * UV) {
+        int sl[UV][DR];
+        Cx<R> x[UV][DR];
+#pragma unroll
+        for (int u = 0; u < UV; ++u) {
+            const int vv = v0 + u * GF_THREADS;
+            if (vv >= nv) continue;
+            const long long a = (long long)base + (long long)vv * DR;   // first arc of the vertex
+            if (pf > 0 && a < (long long)g.A - pf) asm volatile("prefetch.global.L2 [%0];" ::"l"(tin + a + pf));
+            if constexpr (DR == 4) {
+                const int4 q = __ldcs(reinterpret_cast<const int4 *>(srcs + a));
+                sl[u][0] = q.x; sl[u][1] = q.y; sl[u][2] = q.z; sl[u][3] = q.w;
+            } else {
+                const int2 q = __ldcs(reinterpret_cast<const int2 *>(srcs + a));
+                sl[u][0] = q.x; sl[u][1] = q.y;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UV; ++u) {
+            if (v0 + u * GF_THREADS >= nv) continue;
+#pragma unroll
+            for (int i = 0; i < DR; ++i) x[u][i] = ldcg(tin + sl[u][i]);
+        }
+#pragma unroll
+        for (int u = 0; u < UV; ++u) {
+            const int vv = v0 + u * GF_THREADS;
+            if (vv >= nv) continue;
+            const int v = base / DR + vv;
+#pragma unroll
+            for (int i = 0; i < DR; ++i) sm[lpos[v * DR + i]] = coin_row_reg<MODE, DR>(g, x[u], v, i);
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += GF_THREADS) tout[__ldcs(gsl + base + j)] = sm[j];
 }
 
 // Grover pre-pass: the amplitude sum of each heavy vertex (of psi, or of S psi
@@ -548,9 +609,59 @@ qw_status ensure_two_pass(qw_gwalk *g) {
     return QW_OK;
 }
 
+template <class R, int MODE>
+cudaError_t launch_gather_bucket(const qw_gwalk *g, const GraphArgs<R> &a, const Cx<R> *tin, Cx<R> *tout) {
+    const unsigned tiles = (unsigned)(((long long)a.A + GR_TILE - 1) / GR_TILE);
+    if (g->dreg == 2)
+        k_graph_gather_bucket<R, MODE, 2><<<tiles, GF_THREADS, 0, g->stream>>>(a, tin, g->slot_dev, g->lpos_dev,
+                                                                               g->gsl_dev, tout, g->window_arcs);
+    else
+        k_graph_gather_bucket<R, MODE, 4><<<tiles, GF_THREADS, 0, g->stream>>>(a, tin, g->slot_dev, g->lpos_dev,
+                                                                               g->gsl_dev, tout, g->window_arcs);
+    return cudaGetLastError();
+}
+
+// T >= 2 forward steps of the gather form on a regular graph of degree 2 or 4:
+// one bucketing pass from psi, T - 1 fused gather + bucketing passes, one
+// gather into the other state buffer.  The bucketed phi alternates between the
+// two-pass scratch and the input state buffer, which the first pass has
+// consumed.
+template <class R>
+cudaError_t graph_steps_fused(qw_gwalk *g, int64_t T) {
+    GraphArgs<R> a = args_of<R>(g);
+    Cx<R> *in = static_cast<Cx<R> *>(g->buf[g->cur]);
+    Cx<R> *out = static_cast<Cx<R> *>(g->buf[g->cur ^ 1]);
+    Cx<R> *x[2] = {static_cast<Cx<R> *>(g->tmp_dev), in};
+    cudaError_t e;
+    switch (g->mode) {
+        case QW_GCOIN_GROVER: e = launch_bucket<R, QW_GCOIN_GROVER>(g, a, in); break;
+        case QW_GCOIN_UNIFORM: e = launch_bucket<R, QW_GCOIN_UNIFORM>(g, a, in); break;
+        default: e = launch_bucket<R, QW_GCOIN_PER_VERTEX>(g, a, in); break;
+    }
+    for (int64_t t = 1; t < T && e == cudaSuccess; ++t) {
+        const Cx<R> *tin = x[(t - 1) & 1];
+        Cx<R> *tout = x[t & 1];
+        switch (g->mode) {
+            case QW_GCOIN_GROVER: e = launch_gather_bucket<R, QW_GCOIN_GROVER>(g, a, tin, tout); break;
+            case QW_GCOIN_UNIFORM: e = launch_gather_bucket<R, QW_GCOIN_UNIFORM>(g, a, tin, tout); break;
+            default: e = launch_gather_bucket<R, QW_GCOIN_PER_VERTEX>(g, a, tin, tout); break;
+        }
+    }
+    if (e != cudaSuccess) return e;
+    k_graph_gather<R><<<(unsigned)(((long long)a.A + GR_THREADS * GR_GATHER - 1) / (GR_THREADS * GR_GATHER)), GR_THREADS,
+                        0, g->stream>>>(a.A, g->slot_dev, x[(T - 1) & 1], out, g->window_arcs);
+    return cudaGetLastError();
+}
+
 qw_status run_graph(qw_gwalk *g, int64_t T, int adj) {
     if (T < 0) return gfail(g, QW_EINVAL, "T must be >= 0");
     const int kernel = adj ? 2 : (g->variant <= 0 ? 0 : (g->variant == 1 ? 1 : g->variant + 1));
+    if (kernel == 4 && T >= 2 && g->A > 0 && (g->dreg == 2 || g->dreg == 4)) {
+        cudaError_t e = g->prec == QW_F64 ? graph_steps_fused<double>(g, T) : graph_steps_fused<float>(g, T);
+        if (e != cudaSuccess) return gcuda(g, e, "graph step launch");
+        g->cur ^= 1;
+        return QW_OK;
+    }
     for (int64_t t = 0; t < T; ++t) {
         cudaError_t e = g->prec == QW_F64 ? graph_step<double>(g, kernel) : graph_step<float>(g, kernel);
         if (e != cudaSuccess) return gcuda(g, e, "graph step launch");

@@ -106,6 +106,41 @@ def test_all_forms_agree_bitwise(qw, name, window):
         assert np.array_equal(out[0], o)
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("name", ["cycle", "torus", "regular4", "big4"])
+@pytest.mark.parametrize("coin", ["grover", "uniform", "per_vertex"])
+def test_fused_gather_steps_match_single_steps_bitwise(qw, prec, name, coin):
+    """On graphs of degree 2 or 4 the gather form runs a call of T >= 2 steps as
+    one bucketing pass, T - 1 fused gather + bucketing passes and one gather;
+    one step per call runs the two separate passes.  Both feed the coin the
+    same values: identical bits for T = 2, 3 and 8, and the oracle's state."""
+    if name == "big4":   # 3 tiles of 2048 arcs and a ragged fourth; 16 buckets
+        off, partner = inputs.random_regular_arcs(1700, 4, seed=14)
+    else:
+        off, partner = graph(name)
+    rng = np.random.default_rng(5)
+    C = coins_for(coin, off, rng)
+    psi0 = inputs.random_state((int(off[-1]),), seed=43)
+    window = (int(off[-1]) // 16 + 1) * (16 if prec == "f64" else 8)
+    for T in (2, 3, 8):
+        a = qw.GraphWalk(off, partner, prec=prec).set_coin(C).set_state(psi0).set_window(window).set_variant(3)
+        b = qw.GraphWalk(off, partner, prec=prec).set_coin(C).set_state(psi0).set_window(window).set_variant(3)
+        a.step(T)
+        for _ in range(T):
+            b.step(1)
+        sa, sb = a.state(), b.state()
+        assert np.array_equal(sa, sb)
+        want = oracle.graph_evolve(off, partner, psi0, T, coins=C)
+        assert np.abs(sa - want).max() < tol(prec, T, 4)
+        # and a further call continues from the right buffer
+        a.step(2)
+        b.step(1)
+        b.step(1)
+        assert np.array_equal(a.state(), b.state())
+        a.close()
+        b.close()
+
+
 @pytest.mark.parametrize("dims", [(64,), (40, 24), (3, 5)])
 def test_graph_on_lattice_matches_the_lattice_kernels(qw, dims):
     """The lattice as a graph with the lattice's coin slots runs the flip-flop
