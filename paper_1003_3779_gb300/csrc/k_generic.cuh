@@ -243,11 +243,17 @@ k_step_generic_tile(View in, View out, GenGeom g, CoinP<typename St<P>::real> cp
     if (tx >= g.ntx) tx -= g.ntx;
     if (ty >= g.nty) ty -= g.nty;
     const int x0 = tx * GT_X, y0 = ty * GY;
-    for (int i = threadIdx.x; i < EX * EY; i += GT_THREADS) {
-        const int ex = i % EX, ey = i / EX;
+    // item i of the tile and halo is (ex, ey) = (i mod EX, i div EX), advanced
+    // by GT_THREADS items per round without a division
+    constexpr int DX = GT_THREADS % EX, DY = GT_THREADS / EX;
+    int ex = (int)threadIdx.x % EX, ey = (int)threadIdx.x / EX;
+    for (int i = threadIdx.x; i < EX * EY; i += GT_THREADS, ex += DX, ey += DY) {
+        if (ex >= EX) { ex -= EX; ++ey; }
         int gx = x0 - 1 + ex, gy = y0 - 1 + ey;       // in [-1, n + GT_X]: wrap
-        gx = gx < 0 ? gx + nx : (gx >= nx ? gx % nx : gx);
-        gy = gy < 0 ? gy + ny : (gy >= ny ? gy % ny : gy);
+        if (gx < 0) gx += nx;
+        while (gx >= nx) gx -= nx;                    // once, unless the lattice is narrower than a tile
+        if (gy < 0) gy += ny;
+        while (gy >= ny) gy -= ny;
         const int64_t u = (int64_t)gy * nx + gx;
         C a[4], e[4];
 #pragma unroll
