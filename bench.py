@@ -578,19 +578,25 @@ def run_gpu(args, rank, world, local):
         # the n steps from the host input (each copies its 2 GiB in and its P out)
         # with every copy overlapping the neighbouring step's walk
         w.run_host_batch(hin, T_STEPS, count=2, P_out=hP)   # warm-up: allocates the third buffer
-        barrier(dist, local)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        n_pipe = 10   # ten steps (0.8 s): an occasional slow host copy weighs less
-        _, e2e_norms = w.run_host_batch(hin, T_STEPS, count=n_pipe, P_out=hP, norms=True)
-        torch.cuda.synchronize()
-        tp = max_over_ranks(dist, time.perf_counter() - t0, local)
+        n_pipe = 10   # ten steps (0.8 s) per call
+        # three calls, the median reported (a host-side stall, such as the ones the
+        # sequential steps above sometimes meet, lands in one call, not the value)
+        tps, e2e_err = [], 0.0
+        for _ in range(3):
+            barrier(dist, local)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, e2e_norms = w.run_host_batch(hin, T_STEPS, count=n_pipe, P_out=hP, norms=True)
+            torch.cuda.synchronize()
+            tps.append(max_over_ranks(dist, time.perf_counter() - t0, local))
+            e2e_err = max(e2e_err, float(np.abs(e2e_norms - 1).max()))
+        tp = statistics.median(tps)
         e2e = {"value": aggregate_throughput(2.0 * N_SITES * T_STEPS * n_pipe, tp, world),
                "unit": UNIT, "h2d_bytes_per_step": int(hin.nbytes),
                "d2h_bytes_per_step": int(hP.nbytes) + 8, "steps": n_pipe,
-               "calls": "qw_run_host_batch(count = steps): copies overlap the steps",
-               "ms_per_step": 1e3 * tp / n_pipe, "max_norm_err": float(np.abs(e2e_norms - 1).max()),
-               "sequential": sequential}
+               "calls": "qw_run_host_batch(count = steps): copies overlap the steps; median of 3 calls",
+               "ms_per_step": 1e3 * tp / n_pipe, "ms_per_step_of_each_call": [round(1e3 * t / n_pipe, 2) for t in tps],
+               "max_norm_err": e2e_err, "sequential": sequential}
 
     # the torus: the fused 2D step (k = 1) on the 8192^2 lattice, against the HBM roof
     torus = {}

@@ -167,7 +167,7 @@ qw_status qw_probabilities(qw_walk *w, void *P_out, qw_rdtype pdtype, int on_dev
  * layout of qw_set_state; dtype must match the precision (QW_C64 for QW_F32,
  * QW_C128 for QW_F64; else QW_EUNSUPPORTED).  P of run i goes to
  * P_out + i*p_stride bytes (nsites values of pdtype), its norm to norms_out[i]
- * (may be NULL).  A stride of 0 reuses one buffer for every run (the last
+ * (may be NULL; any host memory: the norms are copied once, at the end).  A stride of 0 reuses one buffer for every run (the last
  * run's P remains).  Host buffers should be pinned for the copies to overlap.
  * Synchronous: returns when every P is on the host; the walk's state is then
  * the last run's final state. */

@@ -895,8 +895,14 @@ qw_status qw_run_host_batch(qw_walk *w, int count, const void *amp_in, int64_t i
         if (e != cudaSuccess) return cuda_error(w, e, "pipelined probability buffers");
         w->pipe_p_bytes = pb;
     }
-    if (!w->pipe_norm && (e = dev_alloc((void **)&w->pipe_norm, 2 * sizeof(double))) != cudaSuccess)
-        return cuda_error(w, e, "pipelined norms");
+    if (w->pipe_norm_cap < count) {
+        cudaStreamSynchronize(w->stream);
+        cudaFree(w->pipe_norm);
+        w->pipe_norm = nullptr; w->pipe_norm_cap = 0;
+        if ((e = dev_alloc((void **)&w->pipe_norm, sizeof(double) * (size_t)count)) != cudaSuccess)
+            return cuda_error(w, e, "pipelined norms");
+        w->pipe_norm_cap = count;
+    }
     if (!w->s_in && (e = cudaStreamCreateWithFlags(&w->s_in, cudaStreamNonBlocking)) != cudaSuccess)
         return cuda_error(w, e, "copy stream");
     if (!w->s_out && (e = cudaStreamCreateWithFlags(&w->s_out, cudaStreamNonBlocking)) != cudaSuccess)
@@ -953,13 +959,11 @@ qw_status qw_run_host_batch(qw_walk *w, int count, const void *amp_in, int64_t i
         if ((st = run_steps(w, T, 0)) != QW_OK) break;
         void *pslot = w->pipe_p[i & 1];
         e = launch_marginals(w->prec, cur_view(w), w->ns, pslot, pdtype == QW_R32, w->partials, marginal_blocks(),
-                             w->pipe_norm + (i & 1), w->stream);
+                             w->pipe_norm + i, w->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev_done[i], w->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(w->s_out, ev_done[i], 0);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(static_cast<char *>(P_out) + i * p_stride, pslot, pb, cudaMemcpyDeviceToHost, w->s_out);
-        if (e == cudaSuccess && norms_out)
-            e = cudaMemcpyAsync(norms_out + i, w->pipe_norm + (i & 1), sizeof(double), cudaMemcpyDeviceToHost, w->s_out);
         if (e == cudaSuccess) e = cudaEventRecord(ev_out[i], w->s_out);
         // the run's result is in w->buf[w->cur]; the next run's input is in bufs[z]
         const int res = w->buf[w->cur] == bufs[x] ? x : y;
@@ -984,6 +988,10 @@ qw_status qw_run_host_batch(qw_walk *w, int count, const void *amp_in, int64_t i
     destroy_events();
     if (st != QW_OK) return st;
     if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : e4);
+    // the norms of all runs in one copy once everything is done (norms_out may
+    // be pageable: a copy per run would hold the host until that run ended)
+    if (e == cudaSuccess && norms_out)
+        e = cudaMemcpy(norms_out, w->pipe_norm, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_error(w, e, "pipelined runs");
     return QW_OK;
 }

@@ -58,7 +58,8 @@ struct qw_walk {
     void *buf3 = nullptr;
     void *pipe_p[2] = {nullptr, nullptr};
     size_t pipe_p_bytes = 0;
-    double *pipe_norm = nullptr;
+    double *pipe_norm = nullptr;   // one norm per run of qw_run_host_batch
+    int64_t pipe_norm_cap = 0;
     cudaStream_t s_in = nullptr, s_out = nullptr;
 
     // Light-cone clipping (the growing computation window of a localised walk,

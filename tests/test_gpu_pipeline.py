@@ -80,3 +80,20 @@ def test_pipelined_rejections(qw):
     with pytest.raises(qw.QWError):
         w.run_host_batch(np.zeros((2, 2, 64), dtype=np.complex64), 3)
     w.close()
+
+
+def test_pipelined_norms_when_the_count_grows(qw):
+    """The per-run norms are kept on the device and copied once at the end; a
+    later call with more runs than any before gets a larger array."""
+    N, T = 2000, 15
+    states = np.stack([inputs.random_state((2, N), seed=50 + i).astype(np.complex64) for i in range(7)])
+    w = qw.Walk((N,), prec="f32").set_coin(inputs.su2(0.7))
+    ref = qw.Walk((N,), prec="f32").set_coin(inputs.su2(0.7))
+    for n in (2, 7, 3):
+        _, norms = w.run_host_batch(states[:n], T, norms=True)
+        assert norms.shape == (n,)
+        for i in range(n):
+            ref.set_state(states[i]).step(T)
+            assert norms[i] == ref.probabilities()[1], (n, i)
+    w.close()
+    ref.close()
