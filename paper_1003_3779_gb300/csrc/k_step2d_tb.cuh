@@ -19,9 +19,10 @@
 //   is unrolled by two, so the coin output of row r+1 is written straight
 //   into the set that is free, with no copies -- and plane 2 of rows r and
 //   r-1 (two rows of delay) in a per-warp shared-memory ring of two slots;
-// - diagonal lattice: planes 0 and 2 of rows r and r-1 in the ring, stored
-//   already moved in x; planes 1 and 3 come from the newest row, so nothing
-//   stays in registers.
+// - diagonal lattice: planes 0 and 2 of rows r and r-1, stored already
+//   moved in x, plane 0 in registers (two slots per level, selected by the
+//   row parity, which the unrolled row loop makes a literal) and plane 2 in
+//   the ring; planes 1 and 3 come from the newest row.
 // A slot is read (row r-1) and rewritten (row r+1) by the same lane in the
 // same level, so the ring needs no synchronisation.
 //
@@ -70,9 +71,9 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
 template <int N>
 __device__ __forceinline__ void cp_async_wait_pending() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Planes that pass through the shared-memory delay ring: plane 2 on the axis
-// lattice, planes 0 and 2 on the diagonal one.
-template <int SH> constexpr int tb_delay_planes() { return SH == QW_SHIFT_DIAGONAL ? 2 : 1; }
+// Planes that pass through the shared-memory delay ring: plane 2 on both
+// lattices (the diagonal lattice keeps plane 0's two-row delay in registers).
+template <int SH> constexpr int tb_delay_planes() { return 1; }
 
 // 16-byte units of shared memory per warp: the input ring ([slot][plane][lane])
 // and the delay ring ([level][slot][delayed plane][lane]).
@@ -133,6 +134,16 @@ k_step2d_tb(View in, View out, int64_t nx, int64_t ny, int64_t ox0, int64_t ow, 
         for (int c = 0; c < 2; ++c)
 #pragma unroll
             for (int i = 0; i < R; ++i) { Aa[s][c][i] = czero<real>(); Ab[s][c][i] = czero<real>(); }
+    // diagonal lattice: plane 0 of the rows two and one before the newest, per
+    // level, already moved in x ([level][slot parity], as the ring's slots)
+    constexpr int ND = DIAG ? KT : 1;
+    C D0[ND][2][R];
+#pragma unroll
+    for (int s = 0; s < ND; ++s)
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int i = 0; i < R; ++i) D0[s][q][i] = czero<real>();
     if constexpr (CK == CK_HH) gain = gain * (real)(1.0 / (double)(1u << KT));   // the factors 1/2 of H (x) H
     const bool gain_one = is_one(gain);
 
@@ -241,16 +252,19 @@ k_step2d_tb(View in, View out, int64_t nx, int64_t ny, int64_t ox0, int64_t ow, 
                     Aw[s][1][i] = N[1][i];
                 }
             } else {
-                // planes 0 and 2 enter the ring already moved in x, two rows
+                // planes 0 and 2 are delayed already moved in x, two rows
                 // before they are used, so their shuffles stay off this level's
-                // dependency chain
+                // dependency chain: plane 0 in registers, plane 2 in the ring
+                const int q = (PAR + s) & 1;
                 C s0[R], s2[R];
                 from_left(N[0], s0);           // to (x+1, y+1) two rows on
                 from_right(N[2], s2);          // to (x-1, y+1) two rows on
-                S::unpack(dv[0], psi[0]);      // from (x-1, y-1)
-                S::unpack(dv[1], psi[2]);      // from (x+1, y-1)
-                d[0] = pack2(s0);
-                d[32] = pack2(s2);
+#pragma unroll
+                for (int i = 0; i < R; ++i) psi[0][i] = D0[DIAG ? s : 0][q][i];   // from (x-1, y-1)
+                S::unpack(dv[0], psi[2]);      // from (x+1, y-1)
+#pragma unroll
+                for (int i = 0; i < R; ++i) D0[DIAG ? s : 0][q][i] = s0[i];
+                d[0] = pack2(s2);
                 from_left(N[1], psi[1]);       // from (x-1, y+1)
                 from_right(N[3], psi[3]);      // from (x+1, y+1)
             }
