@@ -6,6 +6,7 @@
 #include "k_step1d.cuh"
 #include "k_step2d.cuh"
 #include "k_generic.cuh"
+#include "k_window1d.cuh"
 
 #include <algorithm>
 
@@ -361,9 +362,56 @@ cudaError_t generic_t(const StepGenericArgs &a, const void *coinp, cudaStream_t 
     return cudaGetLastError();
 }
 
+// The 1D window kernel (a clipped forward walk on the segment or the line,
+// nsteps steps in one CTA); gains[i] is the drift gain of step i, a.rstep the
+// random-link step of the first.  cudaErrorInvalidValue if the window after
+// the steps is wider than win_capacity<P>() or nsteps is out of [1, WIN_MAX_STEPS].
+template <int P, int CK, int SHIFT>
+static cudaError_t gowin_shift(const StepGenericArgs &a, const CoinP<typename St<P>::real> &cp, const double *gains,
+                               int nsteps, cudaStream_t s) {
+    using real = typename St<P>::real;
+    const int64_t w0 = std::max<int64_t>(0, a.bx0 - nsteps), w1 = std::min<int64_t>(a.nx, a.bx0 + a.bw + nsteps);
+    const int64_t wn = w1 - w0;
+    if (nsteps < 1 || nsteps > WIN_MAX_STEPS || wn < 1 || wn > win_capacity<P>() || a.bc == QW_BC_PERIODIC)
+        return cudaErrorInvalidValue;
+    GenGeom g{a.ndim, a.nx, a.ny, a.nx * a.ny, a.shift, a.bc, a.links, a.rthr, a.rk0, a.rk1, a.rstep, 0, 1, 0, 1};
+    WinGains<real> gv{};
+    for (int i = 0; i < nsteps; ++i) gv.v[i] = real_from_double<real>(gains[i]);
+    const bool links = a.links != nullptr || a.rthr != 0;
+    auto kfn = links ? k_step1d_window<P, SHIFT, CK, true> : k_step1d_window<P, SHIFT, CK, false>;
+    static bool attr[2] = {false, false};   // per instantiation of (P, CK, SHIFT, links)
+    if (!attr[links]) {
+        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WIN_SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr[links] = true;
+    }
+    kfn<<<1, WIN_THREADS, win_smem<P>(wn), s>>>(a.in, a.out, g, cp, static_cast<const Cx<real> *>(a.coins), a.phi,
+                                                 (int)a.bx0, (int)a.bw, nsteps, (int)w0, (int)wn, gv);
+    return cudaGetLastError();
+}
+
+template <int P, int CK>
+static cudaError_t gowin(const StepGenericArgs &a, const CoinP<typename St<P>::real> &cp, const double *gains, int nsteps,
+                         cudaStream_t s) {
+    if (a.shift == QW_SHIFT_MOVING) return gowin_shift<P, CK, QW_SHIFT_MOVING>(a, cp, gains, nsteps, s);
+    if (a.shift == QW_SHIFT_FLIPFLOP) return gowin_shift<P, CK, QW_SHIFT_FLIPFLOP>(a, cp, gains, nsteps, s);
+    return cudaErrorInvalidValue;
+}
+
+template <int P>
+cudaError_t window1d_t(const StepGenericArgs &a, const void *coinp, const double *gains, int nsteps, cudaStream_t s) {
+    const auto &cp = *static_cast<const CoinP<typename St<P>::real> *>(coinp);
+    if (a.ndim != 1 || a.adjoint || a.nx >= (int64_t(1) << 30)) return cudaErrorInvalidValue;
+    switch (a.kind) {   // the coins of the 1D tiles: global coins as the full matrix
+        case CK_PERSITE: return gowin<P, CK_PERSITE>(a, cp, gains, nsteps, s);
+        case CK_PHASE: return gowin<P, CK_PHASE>(a, cp, gains, nsteps, s);
+        default: return gowin<P, CK_COMPLEX>(a, cp, gains, nsteps, s);
+    }
+}
+
 }  // namespace qw
 
-// One translation unit per precision defines these three entry points.
+// One translation unit per precision defines these entry points.
 #define QW_DEFINE_STEP_LAUNCHERS(PREC, SUFFIX)                                                          \
     namespace qw {                                                                                      \
     cudaError_t launch_step1d_##SUFFIX(const Step1DArgs &a, const void *cp, int adj, cudaStream_t s) {  \
@@ -375,6 +423,11 @@ cudaError_t generic_t(const StepGenericArgs &a, const void *coinp, cudaStream_t 
     cudaError_t launch_generic_##SUFFIX(const StepGenericArgs &a, const void *cp, cudaStream_t s) {     \
         return generic_t<PREC>(a, cp, s);                                                               \
     }                                                                                                   \
+    cudaError_t launch_window1d_##SUFFIX(const StepGenericArgs &a, const void *cp, const double *gains,  \
+                                         int nsteps, cudaStream_t s) {                                  \
+        return window1d_t<PREC>(a, cp, gains, nsteps, s);                                               \
+    }                                                                                                   \
+    int64_t window1d_capacity_##SUFFIX() { return win_capacity<PREC>(); }                               \
     int tile1d_##SUFFIX(int tile, int kind, int adj) { return tile1d_effective<PREC>(tile, kind, adj); } \
     bool sweep_ok_##SUFFIX(int64_t n, int K, int kind, int tile) { return sweep_ok<PREC>(n, K, kind, tile); } \
     int sweep_tile_##SUFFIX(int64_t n, int tile) { return sweep_tile<PREC>(n, tile); }                   \

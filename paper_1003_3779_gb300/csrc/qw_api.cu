@@ -76,6 +76,26 @@ static cudaError_t step2d(int prec, const Step2DArgs &a, const void *cp, int adj
     }
     return cudaErrorInvalidValue;
 }
+static cudaError_t stepwin(int prec, const StepGenericArgs &a, const void *cp, const double *gains, int nsteps,
+                           cudaStream_t s) {
+    switch (prec) {
+        case QW_F64: return launch_window1d_f64(a, cp, gains, nsteps, s);
+        case QW_F32: return launch_window1d_f32(a, cp, gains, nsteps, s);
+        case QW_F32_BF16STORE: return launch_window1d_bf16(a, cp, gains, nsteps, s);
+        case QW_F32_COMP: return launch_window1d_comp(a, cp, gains, nsteps, s);
+    }
+    return cudaErrorInvalidValue;
+}
+static int64_t window_capacity(int prec) {
+    switch (prec) {
+        case QW_F64: return window1d_capacity_f64();
+        case QW_F32: return window1d_capacity_f32();
+        case QW_F32_BF16STORE: return window1d_capacity_bf16();
+        case QW_F32_COMP: return window1d_capacity_comp();
+    }
+    return 0;
+}
+
 static cudaError_t stepgen(int prec, const StepGenericArgs &a, const void *cp, cudaStream_t s) {
     switch (prec) {
         case QW_F64: return launch_generic_f64(a, cp, s);
@@ -434,7 +454,34 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
         a.rthr = w->link_thr;
         a.rk0 = (uint32_t)w->link_seed; a.rk1 = (uint32_t)(w->link_seed >> 32);
         if (w->kind == CK_SIGN_P || w->kind == CK_SIGN_M) a.kind = CK_COMPLEX;   // generic reads the matrix
+        // a clipped forward walk on the segment or the line: as many steps as keep
+        // the box (after them) within one CTA's window go into one launch
+        const bool win_ok = w->ndim == 1 && !adj && w->bc != QW_BC_PERIODIC &&
+                            (w->shift == QW_SHIFT_MOVING || w->shift == QW_SHIFT_FLIPFLOP) && w->nx < (int64_t(1) << 30);
+        const int64_t win_cap = win_ok ? window_capacity(w->prec) : 0;
         for (int64_t t = 0; t < T; ++t) {
+            if (win_ok && w->sup_mode == 2) {
+                int ns = (int)std::min<int64_t>(T - t, WIN_MAX_STEPS);
+                auto width = [&](int k) {
+                    return std::min<int64_t>(w->nx, w->bx0 + w->bw + k) - std::max<int64_t>(0, w->bx0 - k);
+                };
+                while (ns > 0 && width(ns) > win_cap) --ns;
+                if (ns > 0) {
+                    double gains[WIN_MAX_STEPS];
+                    for (int i = 0; i < ns; ++i) gains[i] = drift_gain(w, 1, t + i + 1 == T);
+                    a.rstep = (uint32_t)w->link_step;   // the first step's; step i draws rstep + i
+                    if (w->link_thr) w->link_step += ns;
+                    a.gain = 1.0;
+                    a.in = cur_view(w); a.out = next_view(w);
+                    a.bx0 = w->bx0; a.bw = w->bw; a.by0 = 0; a.bh = 1;
+                    if ((e = stepwin(w->prec, a, cp, gains, ns, w->stream)) != cudaSuccess)
+                        return cuda_error(w, e, "window step launch");
+                    grow_support(w, ns);
+                    w->cur ^= 1;
+                    t += ns - 1;
+                    continue;
+                }
+            }
             // random links: a forward step draws the mask of its index, then counts
             // up; the adjoint counts down first, so it undoes the last forward step
             if (w->link_thr && adj) --w->link_step;
@@ -990,8 +1037,10 @@ qw_status qw_run_host_batch(qw_walk *w, int count, const void *amp_in, int64_t i
     if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : e4);
     // the norms of all runs in one copy once everything is done (norms_out may
     // be pageable: a copy per run would hold the host until that run ended)
-    if (e == cudaSuccess && norms_out)
-        e = cudaMemcpy(norms_out, w->pipe_norm, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && norms_out) {
+        e = cudaMemcpyAsync(norms_out, w->pipe_norm, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost, w->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
+    }
     if (e != cudaSuccess) return cuda_error(w, e, "pipelined runs");
     return QW_OK;
 }
@@ -1057,6 +1106,12 @@ qw_status qw_describe(const qw_walk *w, char *buf, size_t len) {
     const bool generic = w->bc != QW_BC_PERIODIC || links_on(w) ||
                          (w->ndim == 2 && (w->kind == CK_PERSITE ||
                                            (w->kind == CK_PHASE && !(w->prec == QW_F32 || w->prec == QW_F64))));
+    // a clipped walk on the segment or the line whose box (one step on) fits the
+    // window CTA runs its steps in the window kernel
+    const bool window = generic && w->ndim == 1 && w->bc != QW_BC_PERIODIC && w->sup_mode == 2 &&
+                        (w->shift == QW_SHIFT_MOVING || w->shift == QW_SHIFT_FLIPFLOP) && w->nx < (int64_t(1) << 30) &&
+                        std::min<int64_t>(w->nx, w->bx0 + w->bw + 1) - std::max<int64_t>(0, w->bx0 - 1) <=
+                            window_capacity(w->prec);
     char sup[96];
     if (w->sup_mode == 2)
         std::snprintf(sup, sizeof sup, "[%lld, %lld, %lld, %lld]", (long long)w->bx0, (long long)w->bw,
@@ -1068,7 +1123,7 @@ qw_status qw_describe(const qw_walk *w, char *buf, size_t len) {
                   "\"k\": %d, \"tile\": %d, \"path\": \"%s\", \"state_bytes\": %zu, \"clipping\": %d, "
                   "\"support\": %s}",
                   w->ndim, (long long)w->ns, w->d, w->prec, kinds[w->kind], k, t,
-                  generic ? "generic"
+                  window ? "k_step1d_window" : generic ? "generic"
                           : (w->ndim == 1 ? (var == 1 && w->sup_mode != 2 ? "k_step1d_sweep" : "k_step1d")
                                           : (k > 1 && step2d_tb_ok(w->prec, w->kind, k, w->shift) ? "k_step2d_tb" : "k_step2d")),
                   w->state_bytes, (int)w->clip_on, sup);

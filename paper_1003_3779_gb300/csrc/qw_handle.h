@@ -135,6 +135,14 @@ cudaError_t launch_generic_f32(const StepGenericArgs &, const void *, cudaStream
 cudaError_t launch_generic_f64(const StepGenericArgs &, const void *, cudaStream_t);
 cudaError_t launch_generic_bf16(const StepGenericArgs &, const void *, cudaStream_t);
 cudaError_t launch_generic_comp(const StepGenericArgs &, const void *, cudaStream_t);
+cudaError_t launch_window1d_f32(const StepGenericArgs &, const void *, const double *, int, cudaStream_t);
+cudaError_t launch_window1d_f64(const StepGenericArgs &, const void *, const double *, int, cudaStream_t);
+cudaError_t launch_window1d_bf16(const StepGenericArgs &, const void *, const double *, int, cudaStream_t);
+cudaError_t launch_window1d_comp(const StepGenericArgs &, const void *, const double *, int, cudaStream_t);
+int64_t window1d_capacity_f32();
+int64_t window1d_capacity_f64();
+int64_t window1d_capacity_bf16();
+int64_t window1d_capacity_comp();
 bool sweep_ok_f32(int64_t, int, int, int);
 bool sweep_ok_f64(int64_t, int, int, int);
 bool sweep_ok_bf16(int64_t, int, int, int);

@@ -291,7 +291,9 @@ def test_line_and_segment_window_1d(qw, bc, shift, links, x0):
     on, desc = _generic_run(qw, (N,), psi0, T, True, **kw)
     off, _ = _generic_run(qw, (N,), psi0, T, False, **kw)
     assert same(on, off)
-    assert desc["path"] == ("k_step1d" if bc == 0 and links == "none" else "generic")
+    # the cycle with links: the generic tiles; the segment and the line: the window CTA
+    want_path = ("k_step1d" if links == "none" else "generic") if bc == 0 else "k_step1d_window"
+    assert desc["path"] == want_path
     lo, hi = x0 - T, x0 + T + 1
     if bc == 0:
         assert desc["support"] == [lo % N, 2 * T + 1, 0, 1]
@@ -302,6 +304,84 @@ def test_line_and_segment_window_1d(qw, bc, shift, links, x0):
         closed = oracle.link_masks((N,), seed, p, 0, T)
     want = oracle.evolve(psi0, C, T, shift=shift, bc=bc, closed=closed, closed_per_step=links == "random")
     assert maxabs(on, want) < amp_tol("f32", T)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("bc", [1, 2])
+@pytest.mark.parametrize("links", ["none", "random"])
+def test_window_kernel_launches_ends_and_capacity(qw, prec, bc, links):
+    """The window CTA (segment and line, clipped) runs up to 256 steps per
+    launch.  Calls of 40, 300, 2000 and 7000 steps from x0 = 700 on N = 12000:
+    several launches per call, the box stopping at the left end, random-link
+    steps carried from call to call, and a box that outgrows the CTA's window
+    (about 6200 sites in FP32, 8190 with bfloat16 storage, 3150 in FP64 and
+    double-float), after which the steps go back to the tiled kernel.  Bit for
+    bit against the unclipped steps, and the oracle."""
+    N, x0 = 12000, 700
+    chunks = [40, 300, 2000, 7000]
+    rng = np.random.default_rng(600 + bc)
+    C = inputs.random_unitary(2, rng)
+    psi0 = inputs.localized_1d(N, x0, (0.6, 0.8j))
+    p, seed = (0.05, 93) if links == "random" else (0.0, 0)
+
+    def go(clip):
+        w = qw.Walk((N,), prec=prec, bc=bc).set_clipping(clip).set_coin(C)
+        if p:
+            w.set_link_noise(p, seed)
+        w.set_state(psi0)
+        paths = []
+        for c in chunks:
+            w.step(c)
+            paths.append(w.describe()["path"])
+        out = w.state()
+        w.close()
+        return out, paths
+
+    on, paths = go(True)
+    off, _ = go(False)
+    assert same(on, off)
+    assert paths[0] == "k_step1d_window" and paths[-1] == "generic"
+    T = sum(chunks)
+    closed = oracle.link_masks((N,), seed, p, 0, T) if p else None
+    want = oracle.evolve(psi0, C, T, bc=bc, closed=closed, closed_per_step=bool(p))
+    assert maxabs(on, want) < amp_tol(prec, T)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("kind", ["per_site", "phase"])
+@pytest.mark.parametrize("shift", [0, 1])
+@pytest.mark.parametrize("bc", [1, 2])
+def test_window_kernel_per_site_and_phase_coins(qw, prec, kind, shift, bc):
+    """Per-site coin matrices and phase coins in the window CTA, from the
+    middle of a 4000-site line or segment (T = 600) and from next to its right
+    end (T = 300, the box stops there): clipped and unclipped bit for bit, and
+    the oracle with the same coins."""
+    N = 4000
+    rng = np.random.default_rng(700 + 2 * shift + bc)
+    base = inputs.random_unitary(2, rng)
+    coins = np.stack([inputs.random_unitary(2, rng) for _ in range(N)])
+    phi = rng.uniform(-1, 1, size=(N, 2)).astype(np.float32)
+    for x0, T in ((2000, 600), (3990, 300)):
+        psi0 = inputs.localized_1d(N, x0, (0.6, 0.8j))
+        got = []
+        for clip in (True, False):
+            w = qw.Walk((N,), prec=prec, shift=shift, bc=bc).set_clipping(clip)
+            if kind == "per_site":
+                w.set_coin(coins, per_site=True)
+            else:
+                w.set_coin_phases(base, phi)
+            w.set_state(psi0).step(T)
+            got.append((w.state(), w.describe()["path"]))
+            w.close()
+        assert same(got[0][0], got[1][0]), x0
+        assert got[0][1] == "k_step1d_window"
+        if kind == "per_site":
+            want = oracle.evolve(psi0, coins, T, shift=shift, bc=bc)
+            extra = 0.0
+        else:
+            want = oracle.evolve(psi0, base, T, shift=shift, bc=bc, phi=phi.astype(np.float64))
+            extra = T * 1e-7    # the phases are float inputs
+        assert maxabs(got[0][0], want) < amp_tol(prec, T) + extra, x0
 
 
 @pytest.mark.parametrize("bc", [0, 1, 2])
