@@ -209,7 +209,10 @@ qw_status qw_autotune(qw_walk *w, char *report, size_t report_len);
  * state's nonzero amplitudes on the GPU, and every step kernel then runs only
  * on that box widened by its steps, until the box covers the lattice: on the
  * cycle and the torus the box wraps; on the segment and the line it stops at
- * the ends (with broken links too).  The adjoint with a boundary or broken
+ * the ends (with broken links too), and in 1D, while the box after the next
+ * steps fits one CTA's shared memory (about 6200 sites in FP32), up to 256
+ * steps run in one launch with the state on chip (qw_describe's path
+ * "k_step1d_window").  The adjoint with a boundary or broken
  * links, and per-site coins on the torus, run kernels that step the whole
  * lattice; the box still widens with them.  The first qw_step or
  * qw_step_adjoint after qw_set_state waits for the search (not for other
