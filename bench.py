@@ -885,6 +885,26 @@ def run_case(args):
         gw.close()
         print(json.dumps(out))
         return
+    if args.case == "line":
+        # the paper's line walk: Hadamard coin from the centre of a line of
+        # --n-sites sites (absorbing ends), --steps steps, clipped (the window CTA)
+        n = args.n_sites
+        z = torch.zeros((2, n), dtype=torch.complex64, device="cuda")
+        z[0, n // 2] = 2 ** -0.5
+        z[1, n // 2] = 1j * 2 ** -0.5
+        w = qw.Walk((n,), prec="f32", bc=qw.BC_LINE).set_coin(_in.hadamard())
+        w.set_state(z).step(16)
+        w.set_state(z)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        w.step(args.steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out.update(sites=n, T=args.steps, path=w.describe()["path"], ms=a.elapsed_time(b), norm=w.norm())
+        w.close()
+        print(json.dumps(out))
+        return
     if args.case == "generic":
         # the generic kernel on an L x L torus (--n-sites L, default 4096), Grover,
         # links closed at random afresh at every step (p = 0.05)
@@ -986,7 +1006,7 @@ def main():
                     help="shift of the torus case (2: diagonal lattice, H (x) H; else Grover)")
     ap.add_argument("--coin", default="hadamard_class", choices=["hadamard_class", "real", "complex"],
                     help="coin class of the cycle case")
-    ap.add_argument("--case", default="", choices=["", "cycle", "torus", "batch", "grad", "graph", "generic"],
+    ap.add_argument("--case", default="", choices=["", "cycle", "torus", "batch", "grad", "graph", "generic", "line"],
                     help="run a small named workload for kernel captures instead of the benchmark")
     ap.add_argument("--walks", type=int, default=4096, help="walks of the batch case")
     ap.add_argument("--plan", default="",

@@ -19,6 +19,7 @@
 namespace qw {
 
 constexpr int WIN_THREADS = 1024;
+constexpr int WIN_MAX_STEPS = 256;               // steps per launch
 constexpr size_t WIN_SMEM_BYTES = 200 * 1024;   // dynamic shared memory of the window CTA
 
 // drift gains of the launch's steps, in the compute real

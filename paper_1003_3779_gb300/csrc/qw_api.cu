@@ -461,13 +461,13 @@ qw_status run_steps(qw_walk *w, int64_t T, int adj) {
         const int64_t win_cap = win_ok ? window_capacity(w->prec) : 0;
         for (int64_t t = 0; t < T; ++t) {
             if (win_ok && w->sup_mode == 2) {
-                int ns = (int)std::min<int64_t>(T - t, WIN_MAX_STEPS);
+                int ns = (int)std::min<int64_t>(T - t, WINDOW_MAX_STEPS);
                 auto width = [&](int k) {
                     return std::min<int64_t>(w->nx, w->bx0 + w->bw + k) - std::max<int64_t>(0, w->bx0 - k);
                 };
                 while (ns > 0 && width(ns) > win_cap) --ns;
                 if (ns > 0) {
-                    double gains[WIN_MAX_STEPS];
+                    double gains[WINDOW_MAX_STEPS];
                     for (int i = 0; i < ns; ++i) gains[i] = drift_gain(w, 1, t + i + 1 == T);
                     a.rstep = (uint32_t)w->link_step;   // the first step's; step i draws rstep + i
                     if (w->link_thr) w->link_step += ns;

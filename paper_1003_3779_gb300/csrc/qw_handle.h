@@ -135,6 +135,8 @@ cudaError_t launch_generic_f32(const StepGenericArgs &, const void *, cudaStream
 cudaError_t launch_generic_f64(const StepGenericArgs &, const void *, cudaStream_t);
 cudaError_t launch_generic_bf16(const StepGenericArgs &, const void *, cudaStream_t);
 cudaError_t launch_generic_comp(const StepGenericArgs &, const void *, cudaStream_t);
+// steps per launch of the 1D window kernel (k_window1d.cuh, WIN_MAX_STEPS there)
+constexpr int WINDOW_MAX_STEPS = 256;
 cudaError_t launch_window1d_f32(const StepGenericArgs &, const void *, const double *, int, cudaStream_t);
 cudaError_t launch_window1d_f64(const StepGenericArgs &, const void *, const double *, int, cudaStream_t);
 cudaError_t launch_window1d_bf16(const StepGenericArgs &, const void *, const double *, int, cudaStream_t);

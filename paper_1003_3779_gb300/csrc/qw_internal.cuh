@@ -385,8 +385,6 @@ struct StepGenericArgs {
     int64_t bx0, bw, by0, bh;
 };
 cudaError_t launch_step_generic(int prec, const StepGenericArgs &a, const void *coinp, cudaStream_t s);
-// steps per launch of the 1D window kernel (k_window1d.cuh)
-constexpr int WIN_MAX_STEPS = 256;
 
 // marginals + norm
 cudaError_t launch_marginals(int prec, View v, int64_t nsites, void *P, int p_f32,
