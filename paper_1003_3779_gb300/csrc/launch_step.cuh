@@ -379,12 +379,9 @@ static cudaError_t gowin_shift(const StepGenericArgs &a, const CoinP<typename St
     for (int i = 0; i < nsteps; ++i) gv.v[i] = real_from_double<real>(gains[i]);
     const bool links = a.links != nullptr || a.rthr != 0;
     auto kfn = links ? k_step1d_window<P, SHIFT, CK, true> : k_step1d_window<P, SHIFT, CK, false>;
-    static bool attr[2] = {false, false};   // per instantiation of (P, CK, SHIFT, links)
-    if (!attr[links]) {
-        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WIN_SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        attr[links] = true;
-    }
+    // (set on every launch: the attribute is the current device's, and a launch runs up to 256 steps)
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WIN_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
     kfn<<<1, WIN_THREADS, win_smem<P>(wn), s>>>(a.in, a.out, g, cp, static_cast<const Cx<real> *>(a.coins), a.phi,
                                                  (int)a.bx0, (int)a.bw, nsteps, (int)w0, (int)wn, gv);
     return cudaGetLastError();
